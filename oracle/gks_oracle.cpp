@@ -1,0 +1,1089 @@
+// gks_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// Plain, slow, FP64 CPU oracle of the compact 6th/8th-order gas-kinetic scheme of
+// Zhao, Ji, Shyy & Xu, "Compact higher-order gas-kinetic schemes with spectral-like
+// resolution for compressible flow simulations" (arXiv:1901.00261).
+//
+// Only the test suite, the package smoke check and the benchmark's CPU-baseline leg
+// load this library.  It shares no code, header, table or constant generator with
+// the CUDA library: every coefficient here is derived at start-up from the
+// definitions the paper states, so a reader can check it against the paper by eye.
+//
+//   * compact linear reconstruction: the polynomial conditions of Eq. (recons-8th)
+//     and Eqs. (recons-6th-1)/(recons-6th-2) solved as linear systems (Sec. 3.1);
+//   * WENO-Z sub-stencil candidates: the sub-stencil conditions of Sec. 3.3
+//     solved as linear systems; smoothness indicators by integrating the squared
+//     derivatives, Eq. (smooth-indicator); weights by Eq. (WENO-Z-w) and Eq. (tau);
+//   * the equilibrium state: the Maxwellian of Sec. 2.1; its moments by the
+//     Gaussian recurrences; its derivative coefficients by solving the moment
+//     system with Gaussian elimination;
+//   * the interface distribution function of Eq. (3rd-simplify-flux), integrated
+//     term by term as polynomial moments;
+//   * the two-stage MSMD update of Eqs. (step-hyper-1)/(step-hyper-2) and the
+//     interface-value MSMD plus the Gauss slope formula of Sec. 2.2 / Eq.
+//     (Gausian-formula).
+//
+// Readings taken where the paper is silent or garbled (each one is listed with its
+// reason in the project's design notes):
+//   R1  the Chapman-Enskog bracket uses the physical collision time mu/p (0 for the
+//       Euler equations); the exponentials use the numerical collision time of
+//       Sec. 4 (eps*dt + C|pl-pr|/(pl+pr)*dt, or mu/p + C|pl-pr|/(pl+pr)*dt).
+//       tau_mode = 1 puts the numerical time into the bracket as well.
+//   R2  WENO-Z epsilon defaults to 1e-12.
+//   R3  the beta constant of (a4 h^4)^2 comes from integrating the definition.
+//   R4  interface values: moments of the equilibrium branch of f at t = 0 and its
+//       first two time derivatives.
+//   R5  flux and flux time derivative at the start of a stage: the equilibrium
+//       branch of f is a polynomial in t and is differentiated exactly at t = 0;
+//       the decaying non-equilibrium branch is integrated over [0, dt/2] and
+//       [0, dt] and fitted by a linear function of t (flux_mode = 0).
+//       flux_mode = 1 fits the whole time-integrated flux linearly.
+//   R6  the simplified coefficients a_t, a_xt, a_yt, a_tt lie in span(psi) and are
+//       fixed by the linearised compatibility chain.
+//   R7  non-equilibrium slopes: WENO-weighted candidate derivatives (w1 quadratic).
+//   R8  WENO in the characteristic variables of the normal Jacobian at the mean of
+//       the two cells adjacent to the interface.
+//   R9  tangential direction: quartic through five face line-averages.
+//   R10 Prandtl fix: (1/Pr - 1) times the heat flux of the bracket terms is added
+//       to the energy flux.
+//   R11 1D internal degrees of freedom K = (3 - gamma)/(gamma - 1).
+//   R12 the Maxwellian exponent is negative.
+//   R14 transmissive boundary: ghost cells copy the boundary cell's W and slopes.
+//   R23 the equilibrium state g0 takes its value from the collision of the two initial
+//       states, W0 = int_{u>0} psi g_l + int_{u<0} psi g_r (identical to the linear
+//       reconstruction when the scheme is linear), and its derivatives from the compact
+//       linear reconstruction (eq_mode = 1, default; eq_mode = 0 takes the value from the
+//       linear reconstruction as well).
+
+#include <cmath>
+#include <cstring>
+#include <cstdlib>
+#include <cstdio>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ===========================================================================
+// Dense Gaussian elimination with partial pivoting (n <= 16).
+// A is n x n row-major, B is n x nrhs row-major; B is overwritten by the solution.
+// ===========================================================================
+bool gauss_solve(int n, double* A, double* B, int nrhs) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = std::fabs(A[col * n + col]);
+    for (int r = col + 1; r < n; ++r) {
+      double v = std::fabs(A[r * n + col]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (!(best > 0.0)) return false;
+    if (piv != col) {
+      for (int c = 0; c < n; ++c) { double t = A[col * n + c]; A[col * n + c] = A[piv * n + c]; A[piv * n + c] = t; }
+      for (int c = 0; c < nrhs; ++c) { double t = B[col * nrhs + c]; B[col * nrhs + c] = B[piv * nrhs + c]; B[piv * nrhs + c] = t; }
+    }
+    for (int r = col + 1; r < n; ++r) {
+      double f = A[r * n + col] / A[col * n + col];
+      if (f == 0.0) continue;
+      for (int c = col; c < n; ++c) A[r * n + c] -= f * A[col * n + c];
+      for (int c = 0; c < nrhs; ++c) B[r * nrhs + c] -= f * B[col * nrhs + c];
+    }
+  }
+  for (int row = n - 1; row >= 0; --row) {
+    for (int c = 0; c < nrhs; ++c) {
+      double s = B[row * nrhs + c];
+      for (int k = row + 1; k < n; ++k) s -= A[row * n + k] * B[k * nrhs + c];
+      B[row * nrhs + c] = s / A[row * n + row];
+    }
+  }
+  return true;
+}
+
+double ipow(double x, int p) { double r = 1.0; for (int i = 0; i < p; ++i) r *= x; return r; }
+
+// ===========================================================================
+// Reconstruction geometry (Sec. 3.1, Fig. stencil-1).  Coordinates s = (x - x_i)/dx,
+// so cell I_{i+o} is [o - 1/2, o + 1/2] and the interface x_{i+1/2} is s = 1/2.
+// The 8 stencil inputs are
+//   in[0..3] = W_{i-1}, W_i, W_{i+1}, W_{i+2}
+//   in[4..7] = dx W'_{i-1}, dx W'_i, dx W'_{i+1}, dx W'_{i+2}
+// A polynomial P(s) = sum_p c_p s^p is stored as the matrix C[p][m] of its
+// coefficients as linear functions of the inputs.
+// ===========================================================================
+enum { C_AVG = 0, C_SLOPE = 1 };
+struct Cond { int kind; int cell; };  // cell offset o in {-1,0,1,2}
+
+int cond_input(const Cond& c) { return (c.kind == C_AVG ? 0 : 4) + c.cell + 1; }
+
+// Row of a condition: (1/dx) * int_{I_o} s^p ds for an average, and
+// int_{I_o} d/ds s^p ds = dx * (averaged slope) for a slope condition.
+double cond_row(const Cond& c, int p) {
+  double a = c.cell - 0.5, b = c.cell + 0.5;
+  if (c.kind == C_AVG) return (ipow(b, p + 1) - ipow(a, p + 1)) / (p + 1);
+  return p == 0 ? 0.0 : ipow(b, p) - ipow(a, p);
+}
+
+struct StencilPoly {
+  int deg = 0;
+  double C[8][8] = {};   // C[p][m], p <= deg
+};
+
+// Exactly determined: the deg+1 conditions fix the polynomial (Eq. recons-8th and the
+// sub-stencil conditions of Sec. 3.3).
+StencilPoly fit_exact(int deg, const Cond* conds) {
+  int n = deg + 1;
+  double A[64], B[64 * 8];
+  for (int r = 0; r < n; ++r)
+    for (int p = 0; p < n; ++p) A[r * n + p] = cond_row(conds[r], p);
+  for (int r = 0; r < n; ++r)
+    for (int m = 0; m < 8; ++m) B[r * 8 + m] = (cond_input(conds[r]) == m) ? 1.0 : 0.0;
+  StencilPoly P; P.deg = deg;
+  if (!gauss_solve(n, A, B, 8)) { std::fprintf(stderr, "oracle: singular stencil\n"); std::abort(); }
+  for (int p = 0; p < n; ++p) for (int m = 0; m < 8; ++m) P.C[p][m] = B[p * 8 + m];
+  return P;
+}
+
+// Constrained least squares for P^5 (Eqs. recons-6th-1, recons-6th-2): the conditions on
+// I_i and I_{i+1} hold exactly; those on I_{i-1} and I_{i+2} (averages, and slope
+// integrals in value units as printed) hold in the unweighted least-squares sense.
+// Solved through the KKT system [Al^T Al, Ae^T; Ae, 0][c; mu] = [Al^T bl; be].
+StencilPoly fit_constrained_ls(int deg, const Cond* exact, int ne, const Cond* ls, int nl) {
+  int nc = deg + 1, n = nc + ne;
+  double A[16 * 16], B[16 * 8];
+  std::memset(A, 0, sizeof(A)); std::memset(B, 0, sizeof(B));
+  for (int p = 0; p < nc; ++p)
+    for (int q = 0; q < nc; ++q) {
+      double s = 0.0;
+      for (int r = 0; r < nl; ++r) s += cond_row(ls[r], p) * cond_row(ls[r], q);
+      A[p * n + q] = s;
+    }
+  for (int r = 0; r < ne; ++r)
+    for (int p = 0; p < nc; ++p) { A[p * n + nc + r] = cond_row(exact[r], p); A[(nc + r) * n + p] = cond_row(exact[r], p); }
+  for (int m = 0; m < 8; ++m) {
+    for (int p = 0; p < nc; ++p) {
+      double s = 0.0;
+      for (int r = 0; r < nl; ++r) if (cond_input(ls[r]) == m) s += cond_row(ls[r], p);
+      B[p * 8 + m] = s;
+    }
+    for (int r = 0; r < ne; ++r) B[(nc + r) * 8 + m] = (cond_input(exact[r]) == m) ? 1.0 : 0.0;
+  }
+  StencilPoly P; P.deg = deg;
+  if (!gauss_solve(n, A, B, 8)) { std::fprintf(stderr, "oracle: singular KKT\n"); std::abort(); }
+  for (int p = 0; p < nc; ++p) for (int m = 0; m < 8; ++m) P.C[p][m] = B[p * 8 + m];
+  return P;
+}
+
+// Weights of the q-th derivative (in s) of P at s = x, as linear functionals of the inputs.
+void poly_eval_weights(const StencilPoly& P, double x, int q, double* w) {
+  for (int m = 0; m < 8; ++m) {
+    double s = 0.0;
+    for (int p = q; p <= P.deg; ++p) {
+      double f = 1.0;
+      for (int t = 0; t < q; ++t) f *= (p - t);
+      s += f * P.C[p][m] * ipow(x, p - q);
+    }
+    w[m] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// All stencil-derived tables, built once.
+// ---------------------------------------------------------------------------
+struct Tables {
+  // linear compact reconstruction: [order 6 -> 0, 8 -> 1][value, d/ds, d2/ds2][8]
+  double lin[2][3][8];
+  // WENO candidates 0..6 and w~1 (index 7): polynomial, value and derivative at s=1/2
+  StencilPoly cand[8];
+  double cval[8][8], cder[8][8];
+  // linear weights d^6_k, d^8_k (printed in Sec. 3.3; d1 and d3 are not fixed by the
+  // consistency condition alone because w1 and w3 coincide as point values)
+  double d[2][7];
+  // tangential quartic (Sec. 3.1 end, R9): 5 face line-averages -> value / d/ds / d2/ds2
+  // at the 3 Gauss points
+  double tan_w[3][3][5];
+  double gauss_s[3], gauss_w[3];
+};
+
+Tables build_tables() {
+  Tables T;
+  // P^7: all 8 conditions on I_{i-1..i+2}.
+  Cond c8[8] = {{C_AVG, -1}, {C_AVG, 0}, {C_AVG, 1}, {C_AVG, 2},
+                {C_SLOPE, -1}, {C_SLOPE, 0}, {C_SLOPE, 1}, {C_SLOPE, 2}};
+  StencilPoly P7 = fit_exact(7, c8);
+  // P^5: exact on I_i, I_{i+1}; least squares on I_{i-1}, I_{i+2}.
+  Cond ce[4] = {{C_AVG, 0}, {C_AVG, 1}, {C_SLOPE, 0}, {C_SLOPE, 1}};
+  Cond cl[4] = {{C_AVG, -1}, {C_AVG, 2}, {C_SLOPE, -1}, {C_SLOPE, 2}};
+  StencilPoly P5 = fit_constrained_ls(5, ce, 4, cl, 4);
+  for (int q = 0; q < 3; ++q) {
+    poly_eval_weights(P5, 0.5, q, T.lin[0][q]);
+    poly_eval_weights(P7, 0.5, q, T.lin[1][q]);
+  }
+  // Sub-stencils S0..S6 of Sec. 3.3 and S~1 (cubic used for beta_1).
+  Cond s0[3] = {{C_AVG, -1}, {C_AVG, 0}, {C_SLOPE, -1}};
+  Cond s1[3] = {{C_AVG, -1}, {C_AVG, 0}, {C_AVG, 1}};
+  Cond s2[4] = {{C_AVG, 0}, {C_AVG, 1}, {C_AVG, 2}, {C_SLOPE, 2}};
+  Cond s4[3] = {{C_AVG, 0}, {C_AVG, 1}, {C_AVG, 2}};
+  Cond s5[5] = {{C_AVG, -1}, {C_AVG, 0}, {C_AVG, 1}, {C_SLOPE, -1}, {C_SLOPE, 0}};
+  Cond s6[5] = {{C_AVG, 0}, {C_AVG, 1}, {C_AVG, 2}, {C_SLOPE, 1}, {C_SLOPE, 2}};
+  Cond s1t[4] = {{C_AVG, -1}, {C_AVG, 0}, {C_AVG, 1}, {C_SLOPE, -1}};
+  T.cand[0] = fit_exact(2, s0);
+  T.cand[1] = fit_exact(2, s1);
+  T.cand[2] = fit_exact(3, s2);
+  T.cand[3] = fit_exact(2, s1);   // S3 has the same cells as S1
+  T.cand[4] = fit_exact(2, s4);
+  T.cand[5] = fit_exact(4, s5);
+  T.cand[6] = fit_exact(4, s6);
+  T.cand[7] = fit_exact(3, s1t);
+  for (int k = 0; k < 8; ++k) {
+    poly_eval_weights(T.cand[k], 0.5, 0, T.cval[k]);
+    poly_eval_weights(T.cand[k], 0.5, 1, T.cder[k]);
+  }
+  const double d6[7] = {33.0 / 700, 11.0 / 140, 22.0 / 175, 11.0 / 100, 11.0 / 100, 37.0 / 140, 37.0 / 140};
+  const double d8[7] = {3.0 / 98, 5.0 / 98, 4.0 / 49, 7.0 / 98, 7.0 / 98, 17.0 / 49, 17.0 / 49};
+  for (int k = 0; k < 7; ++k) { T.d[0][k] = d6[k]; T.d[1][k] = d8[k]; }
+  // Three-point Gauss-Legendre rule on a face segment [-1/2, 1/2] (Sec. 2.1).
+  T.gauss_s[0] = -0.5 * std::sqrt(0.6); T.gauss_s[1] = 0.0; T.gauss_s[2] = 0.5 * std::sqrt(0.6);
+  T.gauss_w[0] = 5.0 / 18; T.gauss_w[1] = 8.0 / 18; T.gauss_w[2] = 5.0 / 18;
+  // Tangential quartic: averages over the 5 unit segments centred at -2..2 fix it.
+  {
+    double A[25], B[25];
+    for (int r = 0; r < 5; ++r) {
+      double a = (r - 2) - 0.5, b = (r - 2) + 0.5;
+      for (int p = 0; p < 5; ++p) A[r * 5 + p] = (ipow(b, p + 1) - ipow(a, p + 1)) / (p + 1);
+      for (int m = 0; m < 5; ++m) B[r * 5 + m] = (r == m) ? 1.0 : 0.0;
+    }
+    if (!gauss_solve(5, A, B, 5)) std::abort();
+    for (int g = 0; g < 3; ++g)
+      for (int q = 0; q < 3; ++q)
+        for (int m = 0; m < 5; ++m) {
+          double s = 0.0;
+          for (int p = q; p < 5; ++p) {
+            double f = 1.0;
+            for (int t = 0; t < q; ++t) f *= (p - t);
+            s += f * B[p * 5 + m] * ipow(T.gauss_s[g], p - q);
+          }
+          T.tan_w[g][q][m] = s;
+        }
+  }
+  return T;
+}
+
+const Tables& tables() { static Tables T = build_tables(); return T; }
+
+double dot8(const double* w, const double* in) { double s = 0.0; for (int m = 0; m < 8; ++m) s += w[m] * in[m]; return s; }
+
+// Smoothness indicator, Eq. (smooth-indicator), in s units: sum over q >= 1 of the
+// integral over the cell I_i = [-1/2, 1/2] of (d^q P/ds^q)^2.
+double smoothness(const double* c, int deg) {
+  double beta = 0.0;
+  for (int q = 1; q <= deg; ++q) {
+    double dq[8] = {0};   // coefficients of d^q P / ds^q
+    for (int p = q; p <= deg; ++p) {
+      double f = 1.0;
+      for (int t = 0; t < q; ++t) f *= (p - t);
+      dq[p - q] = f * c[p];
+    }
+    int dd = deg - q;
+    for (int a = 0; a <= dd; ++a)
+      for (int b = 0; b <= dd; ++b) {
+        int e = a + b;   // int_{-1/2}^{1/2} s^e ds
+        if (e % 2) continue;
+        beta += dq[a] * dq[b] * (2.0 * ipow(0.5, e + 1) / (e + 1));
+      }
+  }
+  return beta;
+}
+
+// WENO-Z left state at x_{i+1/2} for one scalar variable (Sec. 3.3, Eqs. right-left,
+// WENO-Z-w, tau).  Returns value and derivative (in s units); optional diagnostics.
+void weno_left(int oi, const double* in, double eps, double* val, double* der,
+               double* delta_out, double* beta_out) {
+  const Tables& T = tables();
+  double v[7], dv[7], beta[7];
+  for (int k = 0; k < 7; ++k) {
+    v[k] = dot8(T.cval[k], in);
+    dv[k] = dot8(T.cder[k], in);
+    int src = (k == 1) ? 7 : k;   // beta_1 from the cubic w~1 (Sec. 3.3)
+    const StencilPoly& P = T.cand[src];
+    double c[8] = {0};
+    for (int p = 0; p <= P.deg; ++p) c[p] = dot8(P.C[p], in);
+    beta[k] = smoothness(c, P.deg);
+  }
+  double Z = std::fabs(3.0 * (beta[0] - beta[4]) + (beta[4] - beta[3]));
+  double alpha[7], asum = 0.0;
+  for (int k = 0; k < 7; ++k) { alpha[k] = T.d[oi][k] * (1.0 + Z / (beta[k] + eps)); asum += alpha[k]; }
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0; k < 7; ++k) {
+    double dk = alpha[k] / asum;
+    s0 += dk * v[k]; s1 += dk * dv[k];
+    if (delta_out) delta_out[k] = dk;
+    if (beta_out) beta_out[k] = beta[k];
+  }
+  *val = s0; *der = s1;
+}
+
+// Right state by mirror symmetry about x_{i+1/2}: cells swap, slopes change sign.
+void weno_right(int oi, const double* in, double eps, double* val, double* der) {
+  double m[8] = {in[3], in[2], in[1], in[0], -in[7], -in[6], -in[5], -in[4]};
+  double d;
+  weno_left(oi, m, eps, val, &d, nullptr, nullptr);
+  *der = -d;
+}
+
+// ===========================================================================
+// Polynomials in (u, v, xi^2) and Maxwellian moments (Sec. 2.1).
+// A Poly is a list of terms c * u^a v^b (xi^2)^k; duplicates are allowed because
+// every use of a Poly is a linear functional.
+// ===========================================================================
+constexpr int MAXU = 10, MAXV = 10, MAXK = 4;
+struct Term { double c; int a, b, k; };
+struct Poly {
+  Term t[512];
+  int n = 0;
+  void add(double c, int a, int b, int k) {
+    if (c == 0.0) return;
+    if (n >= 512 || a > MAXU || b > MAXV || k > MAXK) { std::fprintf(stderr, "oracle: poly overflow\n"); std::abort(); }
+    t[n++] = {c, a, b, k};
+  }
+};
+Poly pmul(const Poly& p, const Poly& q) {
+  Poly r;
+  for (int i = 0; i < p.n; ++i)
+    for (int j = 0; j < q.n; ++j)
+      r.add(p.t[i].c * q.t[j].c, p.t[i].a + q.t[j].a, p.t[i].b + q.t[j].b, p.t[i].k + q.t[j].k);
+  return r;
+}
+Poly pscale(const Poly& p, double s) { Poly r; for (int i = 0; i < p.n; ++i) r.add(p.t[i].c * s, p.t[i].a, p.t[i].b, p.t[i].k); return r; }
+Poly padd(const Poly& p, const Poly& q) { Poly r = p; for (int i = 0; i < q.n; ++i) r.add(q.t[i].c, q.t[i].a, q.t[i].b, q.t[i].k); return r; }
+Poly pmono(double c, int a, int b, int k) { Poly r; r.add(c, a, b, k); return r; }
+
+// psi = (1, u, v, (u^2 + v^2 + xi^2)/2) in 2D and (1, u, (u^2 + xi^2)/2) in 1D.
+Poly psi(int dim, int k) {
+  Poly r;
+  if (k == 0) r.add(1, 0, 0, 0);
+  else if (k == 1) r.add(1, 1, 0, 0);
+  else if (dim == 2 && k == 2) r.add(1, 0, 1, 0);
+  else { r.add(0.5, 2, 0, 0); if (dim == 2) r.add(0.5, 0, 2, 0); r.add(0.5, 0, 0, 1); }
+  return r;
+}
+// a . psi
+Poly lin(int dim, const double* a) {
+  Poly r;
+  for (int k = 0; k < dim + 2; ++k) r = padd(r, pscale(psi(dim, k), a[k]));
+  return r;
+}
+
+// Maxwellian g = rho (lam/pi)^{(K+dim)/2} exp(-lam((u-U)^2 + (v-V)^2 + xi^2)) (Sec. 2.1,
+// exponent sign per R12).  Moments normalised by rho.
+struct Maxw {
+  int dim = 1; double K = 0;
+  double rho = 1, U = 0, V = 0, lam = 1;
+  double mu[MAXU + 1], mup[MAXU + 1], mun[MAXU + 1], mv[MAXV + 1], mx[MAXK + 1];
+};
+enum { SP_FULL = 0, SP_POS = 1, SP_NEG = 2 };
+
+void maxw_moments(Maxw& g) {
+  double var = 1.0 / (2.0 * g.lam);
+  // full-space <u^n>: Gaussian recurrence m_{n+1} = U m_n + n var m_{n-1}
+  g.mu[0] = 1.0; g.mu[1] = g.U;
+  for (int n = 1; n < MAXU; ++n) g.mu[n + 1] = g.U * g.mu[n] + n * var * g.mu[n - 1];
+  // half spaces: same recurrence, started from erfc / exp
+  double sl = std::sqrt(g.lam);
+  double ex = std::exp(-g.lam * g.U * g.U) / (2.0 * std::sqrt(M_PI * g.lam));
+  g.mup[0] = 0.5 * std::erfc(-sl * g.U); g.mup[1] = g.U * g.mup[0] + ex;
+  g.mun[0] = 0.5 * std::erfc(sl * g.U);  g.mun[1] = g.U * g.mun[0] - ex;
+  for (int n = 1; n < MAXU; ++n) {
+    g.mup[n + 1] = g.U * g.mup[n] + n * var * g.mup[n - 1];
+    g.mun[n + 1] = g.U * g.mun[n] + n * var * g.mun[n - 1];
+  }
+  if (g.dim == 2) {
+    g.mv[0] = 1.0; g.mv[1] = g.V;
+    for (int n = 1; n < MAXV; ++n) g.mv[n + 1] = g.V * g.mv[n] + n * var * g.mv[n - 1];
+  } else {
+    g.mv[0] = 1.0;
+    for (int n = 1; n <= MAXV; ++n) g.mv[n] = 0.0;   // no v in 1D (only b = 0 is ever used)
+  }
+  // <xi^{2k}> for K internal degrees of freedom of variance var each
+  g.mx[0] = 1.0;
+  for (int k = 1; k <= MAXK; ++k) g.mx[k] = g.mx[k - 1] * var * (g.K + 2.0 * (k - 1));
+}
+
+// rho * <P> over the chosen velocity half space
+double integrate(const Poly& P, const Maxw& g, int space) {
+  const double* m = space == SP_FULL ? g.mu : (space == SP_POS ? g.mup : g.mun);
+  double s = 0.0;
+  for (int i = 0; i < P.n; ++i) {
+    const Term& t = P.t[i];
+    if (g.dim == 1 && t.b != 0) { std::fprintf(stderr, "oracle: v in 1D\n"); std::abort(); }
+    s += t.c * m[t.a] * g.mv[t.b] * g.mx[t.k];
+  }
+  return g.rho * s;
+}
+// vector of psi-moments  rho <psi_k P>
+void momvec(const Poly& P, const Maxw& g, int space, double* out) {
+  for (int k = 0; k < g.dim + 2; ++k) out[k] = integrate(pmul(psi(g.dim, k), P), g, space);
+}
+
+// Solve rho <psi (a.psi)> = b for a (the Maxwellian derivative coefficients).
+void solve_coef(const Maxw& g, const double* b, double* a) {
+  int n = g.dim + 2;
+  double A[16], B[4];
+  for (int k = 0; k < n; ++k) {
+    for (int l = 0; l < n; ++l) A[k * n + l] = integrate(pmul(psi(g.dim, k), psi(g.dim, l)), g, SP_FULL);
+    B[k] = b[k];
+  }
+  if (!gauss_solve(n, A, B, 1)) { std::fprintf(stderr, "oracle: singular moment matrix\n"); std::abort(); }
+  for (int k = 0; k < n; ++k) a[k] = B[k];
+}
+
+// Time integrals of the exponential terms: E0 = int_0^d e^{-t/tau} dt,
+// E1 = int_0^d t e^{-t/tau} dt (the latter by its series when d/tau < 1).
+void time_integrals(double d, double tau, double* E0, double* E1) {
+  double y = d / tau;
+  *E0 = -tau * std::expm1(-y);
+  double s;
+  if (y < 1.0) {
+    // 1 - e^{-y}(1+y) = sum_{k>=2} (-1)^k (k-1) y^k / k!
+    s = 0.0; double term = y;   // y^k/k! built incrementally
+    for (int k = 2; k < 40; ++k) {
+      term *= y / k;
+      s += ((k % 2) ? -1.0 : 1.0) * (k - 1) * term;
+    }
+  } else {
+    s = 1.0 - std::exp(-y) * (1.0 + y);
+  }
+  *E1 = tau * tau * s;
+}
+
+// ===========================================================================
+// Gas-kinetic evaluation at one interface point (Sec. 2.1, Eq. 3rd-simplify-flux;
+// Sec. 4 collision times).  Local frame: x is the interface normal.
+// ===========================================================================
+struct PointIn {
+  double W0[4], W0x[4], W0y[4], W0xx[4], W0xy[4], W0yy[4];
+  double Wl[4], Wlx[4], Wly[4], Wr[4], Wrx[4], Wry[4];
+};
+struct PointOut {
+  double F[4], Ft[4];       // flux and its time derivative at the start of the stage
+  double W0[4], Wt[4], Wtt[4];   // interface conservative variables and time derivatives
+};
+struct Phys {
+  int dim; double gamma, K, mu, Pr;
+  double eps_tau = 0.01, C_tau = 1.0;
+  int tau_mode = 0, flux_mode = 0, eq_mode = 1;
+};
+
+bool primitives(const Phys& ph, const double* W, Maxw& g) {
+  g.dim = ph.dim; g.K = ph.K;
+  g.rho = W[0];
+  if (!(g.rho > 0.0)) return false;
+  g.U = W[1] / g.rho;
+  g.V = ph.dim == 2 ? W[2] / g.rho : 0.0;
+  double rhoE = W[ph.dim + 1];
+  double p = (ph.gamma - 1.0) * (rhoE - 0.5 * g.rho * (g.U * g.U + g.V * g.V));
+  if (!(p > 0.0)) return false;
+  g.lam = g.rho / (2.0 * p);
+  maxw_moments(g);
+  return true;
+}
+double pressure(const Maxw& g) { return g.rho / (2.0 * g.lam); }
+
+// Half-space moments of the initial non-equilibrium term:
+// int u psi e^{-t/tau} gk [1 - (a1k u + a2k v) t] H  over t in [0, d].
+void noneq_term(const Phys& ph, const Maxw& gk, const double* a1k, const double* a2k, int space,
+                double E0, double E1, double* out) {
+  int dim = ph.dim, n = dim + 2;
+  Poly U1 = pmono(1, 1, 0, 0);
+  Poly slope = pmul(U1, lin(dim, a1k));
+  if (dim == 2) slope = padd(slope, pmul(pmono(1, 0, 1, 0), lin(dim, a2k)));
+  double m0[4], m1[4];
+  momvec(U1, gk, space, m0);
+  momvec(pmul(U1, slope), gk, space, m1);
+  for (int k = 0; k < n; ++k) out[k] = E0 * m0[k] - E1 * m1[k];
+}
+
+bool gks_point(const Phys& ph, const PointIn& in, double dt, PointOut& out) {
+  const int dim = ph.dim, n = dim + 2;
+  Maxw g0, gl, gr;
+  if (!primitives(ph, in.Wl, gl) || !primitives(ph, in.Wr, gr)) return false;
+  double W0c[4];
+  for (int k = 0; k < n; ++k) W0c[k] = in.W0[k];
+  if (ph.eq_mode == 1) {
+    // equilibrium value from the collision of the left and right initial states (R23)
+    double ml[4], mr[4];
+    momvec(pmono(1, 0, 0, 0), gl, SP_POS, ml);
+    momvec(pmono(1, 0, 0, 0), gr, SP_NEG, mr);
+    for (int k = 0; k < n; ++k) W0c[k] = ml[k] + mr[k];
+  }
+  if (!primitives(ph, W0c, g0)) return false;
+  Poly U1 = pmono(1, 1, 0, 0), V1 = pmono(1, 0, 1, 0);
+  double zero[4] = {0, 0, 0, 0};
+
+  // Equilibrium spatial coefficients: <a1> = dW0/dx, <a2> = dW0/dy, second derivatives.
+  double a1[4], a2[4] = {0, 0, 0, 0}, axx[4], axy[4] = {0, 0, 0, 0}, ayy[4] = {0, 0, 0, 0};
+  solve_coef(g0, in.W0x, a1);
+  solve_coef(g0, in.W0xx, axx);
+  if (dim == 2) { solve_coef(g0, in.W0y, a2); solve_coef(g0, in.W0xy, axy); solve_coef(g0, in.W0yy, ayy); }
+
+  // Compatibility chain (R6): <A> = -<a1 u + a2 v>, <a_xt> = -<a_xx u + a_xy v>,
+  // <a_yt> = -<a_xy u + a_yy v>, <a_tt> = -<a_xt u + a_yt v>.
+  auto chain = [&](const double* cx, const double* cy, double* res_moments, double* res_coef) {
+    Poly P = pmul(U1, lin(dim, cx));
+    if (dim == 2) P = padd(P, pmul(V1, lin(dim, cy)));
+    double m[4];
+    momvec(P, g0, SP_FULL, m);
+    for (int k = 0; k < n; ++k) res_moments[k] = -m[k];
+    solve_coef(g0, res_moments, res_coef);
+  };
+  double Wt[4], A[4], Wxt[4], axt[4], Wyt[4], ayt[4] = {0, 0, 0, 0}, Wtt[4], att[4];
+  chain(a1, a2, Wt, A);
+  chain(axx, axy, Wxt, axt);
+  if (dim == 2) chain(axy, ayy, Wyt, ayt);
+  chain(axt, ayt, Wtt, att);
+
+  // Collision times (Sec. 4; reading R1).
+  double p0 = pressure(g0), pl = pressure(gl), pr = pressure(gr);
+  double jump = ph.C_tau * std::fabs((pl - pr) / (pl + pr)) * dt;
+  double tau_phys = ph.mu / p0;
+  double tau_n = (ph.mu > 0.0 ? tau_phys : ph.eps_tau * dt) + jump;
+  double tau_b = ph.tau_mode == 1 ? tau_n : tau_phys;
+
+  // Equilibrium branch of f: g0 [1 + A t + a_tt t^2/2] - tau_b g0 [(a1 u + a2 v + A) + (a_xt u + a_yt v + a_tt) t]
+  Poly S1 = padd(pmul(U1, lin(dim, a1)), lin(dim, A));
+  if (dim == 2) S1 = padd(S1, pmul(V1, lin(dim, a2)));
+  Poly S2 = padd(pmul(U1, lin(dim, axt)), lin(dim, att));
+  if (dim == 2) S2 = padd(S2, pmul(V1, lin(dim, ayt)));
+  double fe0[4], fe1[4], fe2[4], fb1[4], fb2[4];
+  momvec(U1, g0, SP_FULL, fe0);                       // int u psi g0
+  momvec(pmul(U1, lin(dim, A)), g0, SP_FULL, fe1);    // int u psi A g0
+  momvec(pmul(U1, lin(dim, att)), g0, SP_FULL, fe2);  // int u psi a_tt g0
+  momvec(pmul(U1, S1), g0, SP_FULL, fb1);
+  momvec(pmul(U1, S2), g0, SP_FULL, fb2);
+
+  // Prandtl-number fix (R10): q = 1/2 int (u-U)((u-U)^2 + (v-V)^2 + xi^2) (bracket terms).
+  double q1 = 0.0, q2 = 0.0;
+  if (ph.Pr != 1.0 && tau_b > 0.0) {
+    Poly du; du.add(1, 1, 0, 0); du.add(-g0.U, 0, 0, 0);
+    Poly c2 = pmul(du, du);
+    if (dim == 2) { Poly dv; dv.add(1, 0, 1, 0); dv.add(-g0.V, 0, 0, 0); c2 = padd(c2, pmul(dv, dv)); }
+    c2.add(1, 0, 0, 1);
+    Poly hq = pscale(pmul(du, c2), 0.5);
+    q1 = -tau_b * integrate(pmul(hq, S1), g0, SP_FULL);
+    q2 = -tau_b * integrate(pmul(hq, S2), g0, SP_FULL);
+  }
+
+  // Non-equilibrium branch: -e^{-t/tau} g0 [1 - (a1 u + a2 v) t] + initial terms of g_l, g_r.
+  double a1l[4], a2l[4] = {0, 0, 0, 0}, a1r[4], a2r[4] = {0, 0, 0, 0};
+  solve_coef(gl, in.Wlx, a1l);
+  solve_coef(gr, in.Wrx, a1r);
+  if (dim == 2) { solve_coef(gl, in.Wly, a2l); solve_coef(gr, in.Wry, a2r); }
+  double Fne[2][4];
+  const double deltas[2] = {0.5 * dt, dt};
+  for (int s = 0; s < 2; ++s) {
+    double E0, E1;
+    time_integrals(deltas[s], tau_n, &E0, &E1);
+    double t0[4], tl[4], tr[4];
+    noneq_term(ph, g0, a1, a2, SP_FULL, E0, E1, t0);
+    noneq_term(ph, gl, a1l, a2l, SP_POS, E0, E1, tl);
+    noneq_term(ph, gr, a1r, a2r, SP_NEG, E0, E1, tr);
+    for (int k = 0; k < n; ++k) Fne[s][k] = -t0[k] + tl[k] + tr[k];
+  }
+  (void)zero;
+
+  for (int k = 0; k < n; ++k) {
+    double fneq = (4.0 * Fne[0][k] - Fne[1][k]) / dt;
+    double fneq_t = 4.0 * (Fne[1][k] - 2.0 * Fne[0][k]) / (dt * dt);
+    double feq = fe0[k] - tau_b * fb1[k];
+    double feq_t = fe1[k] - tau_b * fb2[k];
+    if (ph.flux_mode == 1) {
+      // R5 alternative: fit the whole time-integrated flux linearly in t.
+      double Fh[2];
+      for (int s = 0; s < 2; ++s) {
+        double d = deltas[s];
+        Fh[s] = fe0[k] * d + fe1[k] * d * d / 2 + fe2[k] * d * d * d / 6
+              - tau_b * (fb1[k] * d + fb2[k] * d * d / 2) + Fne[s][k];
+      }
+      out.F[k] = (4.0 * Fh[0] - Fh[1]) / dt;
+      out.Ft[k] = 4.0 * (Fh[1] - 2.0 * Fh[0]) / (dt * dt);
+    } else {
+      out.F[k] = feq + fneq;
+      out.Ft[k] = feq_t + fneq_t;
+    }
+    out.W0[k] = W0c[k];
+    out.Wt[k] = Wt[k];
+    out.Wtt[k] = Wtt[k];
+  }
+  if (ph.Pr != 1.0 && tau_b > 0.0 && ph.flux_mode == 0) {
+    out.F[n - 1] += (1.0 / ph.Pr - 1.0) * q1;
+    out.Ft[n - 1] += (1.0 / ph.Pr - 1.0) * q2;
+  }
+  return true;
+}
+
+// ===========================================================================
+// Characteristic projection for WENO (R8): right eigenvectors of the Euler flux
+// Jacobian in the interface-normal direction; the left ones by inversion.
+// ===========================================================================
+void euler_right_eigvecs(int dim, double gamma, const double* W, double* R) {
+  int n = dim + 2;
+  double rho = W[0], U = W[1] / rho, V = dim == 2 ? W[2] / rho : 0.0, rhoE = W[n - 1];
+  double p = (gamma - 1.0) * (rhoE - 0.5 * rho * (U * U + V * V));
+  double c = std::sqrt(gamma * p / rho), H = (rhoE + p) / rho;
+  // columns: U - c, U (entropy), [U (shear)], U + c
+  if (dim == 1) {
+    double cols[3][3] = {{1, U - c, H - U * c}, {1, U, 0.5 * U * U}, {1, U + c, H + U * c}};
+    for (int r = 0; r < 3; ++r) for (int k = 0; k < 3; ++k) R[r * 3 + k] = cols[k][r];
+  } else {
+    double cols[4][4] = {{1, U - c, V, H - U * c}, {1, U, V, 0.5 * (U * U + V * V)},
+                         {0, 0, 1, V}, {1, U + c, V, H + U * c}};
+    for (int r = 0; r < 4; ++r) for (int k = 0; k < 4; ++k) R[r * 4 + k] = cols[k][r];
+  }
+}
+
+// ===========================================================================
+// Solver state and the two-stage step.
+// ===========================================================================
+struct Solver {
+  int nx, ny, dim, nv, order, recon, bcx, bcy;
+  double x0, x1, y0, y1, dx, dy, weno_eps;
+  Phys ph;
+  std::vector<double> W, Wx, Wy;   // [nv][ny][nx]
+  int last_error = 0;
+};
+
+inline long cidx(const Solver& S, int v, int j, int i) { return ((long)v * S.ny + j) * S.nx + i; }
+
+int map_index(int i, int n, int bc) {
+  if (bc == 0) { i %= n; if (i < 0) i += n; return i; }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Normal reconstruction at one face from a 4-cell row (Secs. 3.1, 3.3).
+// in8[v][m] stencil inputs per conservative variable; h = cell size.
+// Outputs are line averages over the face: W0, dW0/dn, d2W0/dn2, Wl, dWl/dn, Wr, dWr/dn.
+struct FaceRecon { double W0[4], W0n[4], W0nn[4], Wl[4], Wln[4], Wr[4], Wrn[4]; };
+
+void normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& fr) {
+  const Tables& T = tables();
+  int oi = S.order == 6 ? 0 : 1, n = S.nv;
+  for (int v = 0; v < n; ++v) {
+    fr.W0[v] = dot8(T.lin[oi][0], in8[v]);
+    fr.W0n[v] = dot8(T.lin[oi][1], in8[v]) / h;
+    fr.W0nn[v] = dot8(T.lin[oi][2], in8[v]) / (h * h);
+  }
+  if (S.recon == 0) {
+    for (int v = 0; v < n; ++v) { fr.Wl[v] = fr.Wr[v] = fr.W0[v]; fr.Wln[v] = fr.Wrn[v] = fr.W0n[v]; }
+    return;
+  }
+  // characteristic projection at the mean of the two cells next to the face
+  double Wm[4], R[16], L[16];
+  for (int v = 0; v < n; ++v) Wm[v] = 0.5 * (in8[v][1] + in8[v][2]);
+  euler_right_eigvecs(S.dim, S.ph.gamma, Wm, R);
+  {
+    double A[16];
+    std::memcpy(A, R, sizeof(double) * n * n);
+    for (int r = 0; r < n; ++r) for (int c = 0; c < n; ++c) L[r * n + c] = (r == c) ? 1.0 : 0.0;
+    if (!gauss_solve(n, A, L, n)) std::abort();
+  }
+  double q[4][8];
+  for (int k = 0; k < n; ++k)
+    for (int m = 0; m < 8; ++m) {
+      double s = 0.0;
+      for (int v = 0; v < n; ++v) s += L[k * n + v] * in8[v][m];
+      q[k][m] = s;
+    }
+  double ql[4], qld[4], qr[4], qrd[4];
+  for (int k = 0; k < n; ++k) {
+    weno_left(oi, q[k], S.weno_eps, &ql[k], &qld[k], nullptr, nullptr);
+    weno_right(oi, q[k], S.weno_eps, &qr[k], &qrd[k]);
+  }
+  for (int v = 0; v < n; ++v) {
+    double a = 0, b = 0, c = 0, d = 0;
+    for (int k = 0; k < n; ++k) {
+      a += R[v * n + k] * ql[k]; b += R[v * n + k] * qld[k];
+      c += R[v * n + k] * qr[k]; d += R[v * n + k] * qrd[k];
+    }
+    fr.Wl[v] = a; fr.Wln[v] = b / h; fr.Wr[v] = c; fr.Wrn[v] = d / h;
+  }
+}
+
+// Per-face results of one stage, Gauss-averaged over the face.
+struct FaceOut { double F[4], Ft[4], W0[4], Wt[4], Wtt[4]; };
+
+// Swap the two velocity components (x-face <-> y-face local frame).
+void swapuv(int dim, double* w) { if (dim == 2) { double t = w[1]; w[1] = w[2]; w[2] = t; } }
+
+// One stage: all x faces (and y faces in 2D) of state (W, Wx, Wy).
+bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<double>& Wx,
+                const std::vector<double>& Wy, double dt,
+                std::vector<FaceOut>& fx, std::vector<FaceOut>& fy) {
+  const Tables& T = tables();
+  const int nx = S.nx, ny = S.ny, n = S.nv, dim = S.dim;
+  bool ok = true;
+
+  // ---- x faces: face f at x_{f-1/2}, f = 0..nx, rows j = 0..ny-1 ----
+  std::vector<FaceRecon> rx((size_t)(nx + 1) * ny);
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < (long)(nx + 1) * ny; ++idx) {
+    int f = (int)(idx % (nx + 1)), j = (int)(idx / (nx + 1));
+    double in8[4][8];
+    for (int v = 0; v < n; ++v)
+      for (int o = 0; o < 4; ++o) {
+        int ci = map_index(f - 2 + o, nx, S.bcx);
+        in8[v][o] = W[cidx(S, v, j, ci)];
+        in8[v][4 + o] = S.dx * Wx[cidx(S, v, j, ci)];
+      }
+    normal_recon(S, in8, S.dx, rx[idx]);
+  }
+  fx.assign((size_t)(nx + 1) * ny, FaceOut());
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < (long)(nx + 1) * ny; ++idx) {
+    int f = (int)(idx % (nx + 1)), j = (int)(idx / (nx + 1));
+    FaceOut& fo = fx[idx];
+    std::memset(&fo, 0, sizeof(fo));
+    int ng = dim == 2 ? 3 : 1;
+    for (int g = 0; g < ng; ++g) {
+      PointIn pin; std::memset(&pin, 0, sizeof(pin));
+      double wgt = 1.0;
+      if (dim == 1) {
+        const FaceRecon& r = rx[idx];
+        for (int v = 0; v < n; ++v) {
+          pin.W0[v] = r.W0[v]; pin.W0x[v] = r.W0n[v]; pin.W0xx[v] = r.W0nn[v];
+          pin.Wl[v] = r.Wl[v]; pin.Wlx[v] = r.Wln[v]; pin.Wr[v] = r.Wr[v]; pin.Wrx[v] = r.Wrn[v];
+        }
+      } else {
+        wgt = T.gauss_w[g];
+        const FaceRecon* rr[5];
+        for (int t = 0; t < 5; ++t) rr[t] = &rx[(size_t)map_index(j - 2 + t, ny, S.bcy) * (nx + 1) + f];
+        const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
+        for (int v = 0; v < n; ++v) {
+          for (int t = 0; t < 5; ++t) {
+            const FaceRecon& r = *rr[t];
+            pin.W0[v] += wv[t] * r.W0[v];
+            pin.W0y[v] += wd[t] * r.W0[v] / S.dy;
+            pin.W0yy[v] += wdd[t] * r.W0[v] / (S.dy * S.dy);
+            pin.W0x[v] += wv[t] * r.W0n[v];
+            pin.W0xy[v] += wd[t] * r.W0n[v] / S.dy;
+            pin.W0xx[v] += wv[t] * r.W0nn[v];
+            pin.Wl[v] += wv[t] * r.Wl[v]; pin.Wly[v] += wd[t] * r.Wl[v] / S.dy; pin.Wlx[v] += wv[t] * r.Wln[v];
+            pin.Wr[v] += wv[t] * r.Wr[v]; pin.Wry[v] += wd[t] * r.Wr[v] / S.dy; pin.Wrx[v] += wv[t] * r.Wrn[v];
+          }
+        }
+      }
+      PointOut po;
+      if (!gks_point(S.ph, pin, dt, po)) {
+#pragma omp critical
+        ok = false;
+        continue;
+      }
+      for (int v = 0; v < n; ++v) {
+        fo.F[v] += wgt * po.F[v]; fo.Ft[v] += wgt * po.Ft[v];
+        fo.W0[v] += wgt * po.W0[v]; fo.Wt[v] += wgt * po.Wt[v]; fo.Wtt[v] += wgt * po.Wtt[v];
+      }
+    }
+  }
+  if (dim == 1) return ok;
+
+  // ---- y faces: face f at y_{f-1/2}, f = 0..ny, columns i = 0..nx-1.  Evaluated in the
+  // local frame where the face normal is the first axis (velocity components swapped). ----
+  std::vector<FaceRecon> ry((size_t)(ny + 1) * nx);
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < (long)(ny + 1) * nx; ++idx) {
+    int i = (int)(idx % nx), f = (int)(idx / nx);
+    double in8[4][8];
+    for (int o = 0; o < 4; ++o) {
+      int cj = map_index(f - 2 + o, ny, S.bcy);
+      double w[4], wy[4];
+      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, cj, i)]; wy[v] = Wy[cidx(S, v, cj, i)]; }
+      swapuv(dim, w); swapuv(dim, wy);
+      for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dy * wy[v]; }
+    }
+    normal_recon(S, in8, S.dy, ry[idx]);
+  }
+  fy.assign((size_t)(ny + 1) * nx, FaceOut());
+#pragma omp parallel for schedule(static)
+  for (long idx = 0; idx < (long)(ny + 1) * nx; ++idx) {
+    int i = (int)(idx % nx), f = (int)(idx / nx);
+    FaceOut& fo = fy[idx];
+    std::memset(&fo, 0, sizeof(fo));
+    for (int g = 0; g < 3; ++g) {
+      PointIn pin; std::memset(&pin, 0, sizeof(pin));
+      double wgt = T.gauss_w[g];
+      const FaceRecon* rr[5];
+      for (int t = 0; t < 5; ++t) rr[t] = &ry[(size_t)f * nx + map_index(i - 2 + t, nx, S.bcx)];
+      const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
+      for (int v = 0; v < n; ++v)
+        for (int t = 0; t < 5; ++t) {
+          const FaceRecon& r = *rr[t];
+          pin.W0[v] += wv[t] * r.W0[v];
+          pin.W0y[v] += wd[t] * r.W0[v] / S.dx;
+          pin.W0yy[v] += wdd[t] * r.W0[v] / (S.dx * S.dx);
+          pin.W0x[v] += wv[t] * r.W0n[v];
+          pin.W0xy[v] += wd[t] * r.W0n[v] / S.dx;
+          pin.W0xx[v] += wv[t] * r.W0nn[v];
+          pin.Wl[v] += wv[t] * r.Wl[v]; pin.Wly[v] += wd[t] * r.Wl[v] / S.dx; pin.Wlx[v] += wv[t] * r.Wln[v];
+          pin.Wr[v] += wv[t] * r.Wr[v]; pin.Wry[v] += wd[t] * r.Wr[v] / S.dx; pin.Wrx[v] += wv[t] * r.Wrn[v];
+        }
+      PointOut po;
+      if (!gks_point(S.ph, pin, dt, po)) {
+#pragma omp critical
+        ok = false;
+        continue;
+      }
+      swapuv(dim, po.F); swapuv(dim, po.Ft); swapuv(dim, po.W0); swapuv(dim, po.Wt); swapuv(dim, po.Wtt);
+      for (int v = 0; v < n; ++v) {
+        fo.F[v] += wgt * po.F[v]; fo.Ft[v] += wgt * po.Ft[v];
+        fo.W0[v] += wgt * po.W0[v]; fo.Wt[v] += wgt * po.Wt[v]; fo.Wtt[v] += wgt * po.Wtt[v];
+      }
+    }
+  }
+  return ok;
+}
+
+// Two-stage fourth-order MSMD step for W (Eqs. step-hyper-1/2) and for the interface
+// distribution function, with the Gauss formula for the slopes (Sec. 2.2, Eq.
+// Gausian-formula).
+int solver_step(Solver& S, double dt) {
+  const int nx = S.nx, ny = S.ny, n = S.nv, dim = S.dim;
+  const long ncell = (long)nx * ny;
+  std::vector<FaceOut> fx1, fy1, fx2, fy2;
+  if (!eval_faces(S, S.W, S.Wx, S.Wy, dt, fx1, fy1)) return -4;
+
+  std::vector<double> Ws(S.W.size()), Wxs(S.Wx.size()), Wys(S.Wy.size());
+  std::vector<double> L(S.W.size()), Lt(S.W.size());
+  for (int v = 0; v < n; ++v)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = cidx(S, v, j, i);
+        const FaceOut& xl = fx1[(size_t)j * (nx + 1) + i];
+        const FaceOut& xr = fx1[(size_t)j * (nx + 1) + i + 1];
+        double l = -(xr.F[v] - xl.F[v]) / S.dx;
+        double lt = -(xr.Ft[v] - xl.Ft[v]) / S.dx;
+        if (dim == 2) {
+          const FaceOut& yb = fy1[(size_t)j * nx + i];
+          const FaceOut& yt = fy1[(size_t)(j + 1) * nx + i];
+          l += -(yt.F[v] - yb.F[v]) / S.dy;
+          lt += -(yt.Ft[v] - yb.Ft[v]) / S.dy;
+        }
+        L[c] = l; Lt[c] = lt;
+        Ws[c] = S.W[c] + 0.5 * dt * l + 0.125 * dt * dt * lt;
+        // interface values at t* = t^n + dt/2: W0 + dt/2 W_t + dt^2/8 W_tt
+        double wr = xr.W0[v] + 0.5 * dt * xr.Wt[v] + 0.125 * dt * dt * xr.Wtt[v];
+        double wl = xl.W0[v] + 0.5 * dt * xl.Wt[v] + 0.125 * dt * dt * xl.Wtt[v];
+        Wxs[c] = (wr - wl) / S.dx;
+        if (dim == 2) {
+          const FaceOut& yb = fy1[(size_t)j * nx + i];
+          const FaceOut& yt = fy1[(size_t)(j + 1) * nx + i];
+          double wt = yt.W0[v] + 0.5 * dt * yt.Wt[v] + 0.125 * dt * dt * yt.Wtt[v];
+          double wb = yb.W0[v] + 0.5 * dt * yb.Wt[v] + 0.125 * dt * dt * yb.Wtt[v];
+          Wys[c] = (wt - wb) / S.dy;
+        }
+      }
+  if (!eval_faces(S, Ws, Wxs, Wys, dt, fx2, fy2)) return -4;
+
+  for (int v = 0; v < n; ++v)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = cidx(S, v, j, i);
+        const FaceOut& xl = fx1[(size_t)j * (nx + 1) + i];
+        const FaceOut& xr = fx1[(size_t)j * (nx + 1) + i + 1];
+        const FaceOut& xl2 = fx2[(size_t)j * (nx + 1) + i];
+        const FaceOut& xr2 = fx2[(size_t)j * (nx + 1) + i + 1];
+        double lt2 = -(xr2.Ft[v] - xl2.Ft[v]) / S.dx;
+        if (dim == 2) {
+          const FaceOut& yb2 = fy2[(size_t)j * nx + i];
+          const FaceOut& yt2 = fy2[(size_t)(j + 1) * nx + i];
+          lt2 += -(yt2.Ft[v] - yb2.Ft[v]) / S.dy;
+        }
+        double Wn = S.W[c] + dt * L[c] + dt * dt / 6.0 * (Lt[c] + 2.0 * lt2);
+        // interface values at t^{n+1}: W0 + dt W_t + dt^2/6 (W_tt + 2 W_tt*)
+        double wr = xr.W0[v] + dt * xr.Wt[v] + dt * dt / 6.0 * (xr.Wtt[v] + 2.0 * xr2.Wtt[v]);
+        double wl = xl.W0[v] + dt * xl.Wt[v] + dt * dt / 6.0 * (xl.Wtt[v] + 2.0 * xl2.Wtt[v]);
+        double wx = (wr - wl) / S.dx;
+        double wy = 0.0;
+        if (dim == 2) {
+          const FaceOut& yb = fy1[(size_t)j * nx + i];
+          const FaceOut& yt = fy1[(size_t)(j + 1) * nx + i];
+          const FaceOut& yb2 = fy2[(size_t)j * nx + i];
+          const FaceOut& yt2 = fy2[(size_t)(j + 1) * nx + i];
+          double wt = yt.W0[v] + dt * yt.Wt[v] + dt * dt / 6.0 * (yt.Wtt[v] + 2.0 * yt2.Wtt[v]);
+          double wb = yb.W0[v] + dt * yb.Wt[v] + dt * dt / 6.0 * (yb.Wtt[v] + 2.0 * yb2.Wtt[v]);
+          wy = (wt - wb) / S.dy;
+        }
+        S.W[c] = Wn; S.Wx[c] = wx;
+        if (dim == 2) S.Wy[c] = wy;
+      }
+  (void)ncell;
+  return 0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (loaded with ctypes by the tests).
+// ===========================================================================
+extern "C" {
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Linear compact reconstruction weights for order 6 or 8: out[3][8] = value, d/ds, d2/ds2
+// at the interface s = 1/2 against (W_{i-1..i+2}, dx W'_{i-1..i+2}).
+int orc_linear_weights(int order, double* out) {
+  if (order != 6 && order != 8) return -1;
+  const Tables& T = tables();
+  std::memcpy(out, T.lin[order == 6 ? 0 : 1], sizeof(double) * 24);
+  return 0;
+}
+
+// Candidate k (0..6; 7 = w~1): out[5][8] polynomial coefficients c_p (s units, origin at
+// the centre of cell i) as linear functions of the 8 inputs; returns the degree.
+int orc_candidate(int k, double* out) {
+  if (k < 0 || k > 7) return -1;
+  const Tables& T = tables();
+  for (int p = 0; p < 5; ++p) for (int m = 0; m < 8; ++m) out[p * 8 + m] = p <= T.cand[k].deg ? T.cand[k].C[p][m] : 0.0;
+  return T.cand[k].deg;
+}
+
+double orc_smoothness(const double* c, int deg) { return smoothness(c, deg); }
+
+// WENO-Z left state for one scalar stencil (Sec. 3.3): out = [value, d/ds, delta[7], beta[7]]
+int orc_weno_left(int order, const double* in8, double eps, double* out) {
+  if (order != 6 && order != 8) return -1;
+  weno_left(order == 6 ? 0 : 1, in8, eps, &out[0], &out[1], out + 2, out + 9);
+  return 0;
+}
+int orc_weno_right(int order, const double* in8, double eps, double* out) {
+  if (order != 6 && order != 8) return -1;
+  weno_right(order == 6 ? 0 : 1, in8, eps, &out[0], &out[1]);
+  return 0;
+}
+
+// Tangential quartic weights out[3 gauss][3 (value, d/ds, d2/ds2)][5]; gauss points and weights.
+void orc_tangential_weights(double* out, double* gs, double* gw) {
+  const Tables& T = tables();
+  std::memcpy(out, T.tan_w, sizeof(double) * 45);
+  for (int g = 0; g < 3; ++g) { gs[g] = T.gauss_s[g]; gw[g] = T.gauss_w[g]; }
+}
+
+// Maxwellian moments normalised by rho: mu/mup/mun[0..MAXU], mv[0..MAXV], mx[0..MAXK].
+void orc_maxwell_moments(int dim, double K, double U, double V, double lam,
+                         double* mu, double* mup, double* mun, double* mv, double* mx) {
+  Maxw g; g.dim = dim; g.K = K; g.rho = 1.0; g.U = U; g.V = V; g.lam = lam;
+  maxw_moments(g);
+  std::memcpy(mu, g.mu, sizeof(g.mu)); std::memcpy(mup, g.mup, sizeof(g.mup));
+  std::memcpy(mun, g.mun, sizeof(g.mun)); std::memcpy(mv, g.mv, sizeof(g.mv));
+  std::memcpy(mx, g.mx, sizeof(g.mx));
+}
+int orc_moment_max(int which) { return which == 0 ? MAXU : (which == 1 ? MAXV : MAXK); }
+
+// Coefficients a (a.psi) of a derivative b of the conservative variables for the
+// Maxwellian (rho, U, V, lam).
+void orc_solve_coef(int dim, double K, double rho, double U, double V, double lam,
+                    const double* b, double* a) {
+  Maxw g; g.dim = dim; g.K = K; g.rho = rho; g.U = U; g.V = V; g.lam = lam;
+  maxw_moments(g);
+  solve_coef(g, b, a);
+}
+
+// rho <psi u^a v^b xi^{2k} (c . psi)> helper for tests: moments of (c.psi) u^a v^b.
+void orc_moment_lin(int dim, double K, double rho, double U, double V, double lam,
+                    const double* c, int a, int b, int space, double* out) {
+  Maxw g; g.dim = dim; g.K = K; g.rho = rho; g.U = U; g.V = V; g.lam = lam;
+  maxw_moments(g);
+  momvec(pmul(pmono(1, a, b, 0), lin(dim, c)), g, space, out);
+}
+
+void orc_time_integrals(double d, double tau, double* E0, double* E1) { time_integrals(d, tau, E0, E1); }
+
+void orc_eigvecs(int dim, double gamma, const double* W, double* R) { euler_right_eigvecs(dim, gamma, W, R); }
+
+// One interface point: pin[12][4] in the order W0, W0x, W0y, W0xx, W0xy, W0yy, Wl, Wlx,
+// Wly, Wr, Wrx, Wry; out[5][4] = F, Ft, W0, Wt, Wtt.  Returns 0 or -4 (non-physical).
+int orc_point(int dim, double gamma, double mu, double Pr, int tau_mode, int flux_mode,
+              const double* pin, double dt, double* out) {
+  Phys ph; ph.dim = dim; ph.gamma = gamma; ph.mu = mu; ph.Pr = Pr;
+  ph.K = dim == 1 ? (3.0 - gamma) / (gamma - 1.0) : (4.0 - 2.0 * gamma) / (gamma - 1.0);
+  ph.tau_mode = tau_mode; ph.flux_mode = flux_mode;
+  PointIn in; std::memcpy(&in, pin, sizeof(in));
+  PointOut po;
+  if (!gks_point(ph, in, dt, po)) return -4;
+  std::memcpy(out, &po, sizeof(po));
+  return 0;
+}
+
+void* orc_create(int nx, int ny, double gamma, double mu, double Pr, int order, int recon,
+                 int bc_x, int bc_y, double x0, double x1, double y0, double y1,
+                 double weno_eps, int tau_mode, int flux_mode) {
+  if (nx < 5 || ny < 1 || (ny > 1 && ny < 5)) return nullptr;
+  if (order != 6 && order != 8) return nullptr;
+  if (recon != 0 && recon != 1) return nullptr;
+  if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return nullptr;
+  if (!(x1 > x0) || (ny > 1 && !(y1 > y0))) return nullptr;
+  Solver* S = new Solver();
+  S->nx = nx; S->ny = ny; S->dim = ny > 1 ? 2 : 1; S->nv = S->dim + 2;
+  S->order = order; S->recon = recon; S->bcx = bc_x; S->bcy = bc_y;
+  S->x0 = x0; S->x1 = x1; S->y0 = y0; S->y1 = y1;
+  S->dx = (x1 - x0) / nx; S->dy = S->dim == 2 ? (y1 - y0) / ny : 1.0;
+  S->weno_eps = weno_eps;
+  S->ph.dim = S->dim; S->ph.gamma = gamma; S->ph.mu = mu; S->ph.Pr = Pr;
+  S->ph.K = S->dim == 1 ? (3.0 - gamma) / (gamma - 1.0) : (4.0 - 2.0 * gamma) / (gamma - 1.0);
+  S->ph.tau_mode = tau_mode; S->ph.flux_mode = flux_mode;
+  size_t sz = (size_t)S->nv * ny * nx;
+  S->W.assign(sz, 0.0); S->Wx.assign(sz, 0.0); S->Wy.assign(S->dim == 2 ? sz : 0, 0.0);
+  return S;
+}
+void orc_destroy(void* h) { delete static_cast<Solver*>(h); }
+// Reading of the equilibrium interface value: 0 = linear compact reconstruction,
+// 1 = collision of the left/right initial states.
+void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; }
+void orc_set_state(void* h, const double* W, const double* Wx, const double* Wy) {
+  Solver* S = static_cast<Solver*>(h);
+  std::memcpy(S->W.data(), W, sizeof(double) * S->W.size());
+  std::memcpy(S->Wx.data(), Wx, sizeof(double) * S->Wx.size());
+  if (S->dim == 2 && Wy) std::memcpy(S->Wy.data(), Wy, sizeof(double) * S->Wy.size());
+}
+void orc_get_state(void* h, double* W, double* Wx, double* Wy) {
+  Solver* S = static_cast<Solver*>(h);
+  std::memcpy(W, S->W.data(), sizeof(double) * S->W.size());
+  std::memcpy(Wx, S->Wx.data(), sizeof(double) * S->Wx.size());
+  if (S->dim == 2 && Wy) std::memcpy(Wy, S->Wy.data(), sizeof(double) * S->Wy.size());
+}
+int orc_step(void* h, double dt) {
+  Solver* S = static_cast<Solver*>(h);
+  if (!(dt > 0.0)) return -1;
+  return solver_step(*S, dt);
+}
+
+// max over cells of (|U| + c)/dx (+ (|V| + c)/dy in 2D), for the CFL time step.
+double orc_max_wavespeed(void* h) {
+  Solver* S = static_cast<Solver*>(h);
+  double m = 0.0;
+  long nc = (long)S->nx * S->ny;
+  for (long c = 0; c < nc; ++c) {
+    double rho = S->W[c], U = S->W[nc + c] / rho;
+    double V = S->dim == 2 ? S->W[2 * nc + c] / rho : 0.0;
+    double rhoE = S->W[(S->nv - 1) * nc + c];
+    double p = (S->ph.gamma - 1.0) * (rhoE - 0.5 * rho * (U * U + V * V));
+    double cs = std::sqrt(S->ph.gamma * p / rho);
+    double s = (std::fabs(U) + cs) / S->dx;
+    if (S->dim == 2) s += (std::fabs(V) + cs) / S->dy;
+    if (s > m) m = s;
+  }
+  return m;
+}
+
+}  // extern "C"

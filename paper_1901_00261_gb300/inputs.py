@@ -1,0 +1,365 @@
+"""Seeded synthetic inputs: initial cell averages and cell-averaged gradients.
+
+This module holds none of the scheme's arithmetic.  It turns point-wise initial
+conditions into the state the scheme evolves -- conservative cell averages W and
+cell-averaged gradients W_x (W_y) -- and evaluates exact solutions for error norms.
+Both the GPU library's tests/benchmark and the CPU oracle's tests take their inputs
+from here.
+
+Layout of every state array: C-contiguous float64 ``[nvar][ny][nx]`` with
+nvar = 3 (1D: rho, rho U, rho E) or 4 (2D: rho, rho U, rho V, rho E).
+
+Cell averages use Gauss-Legendre quadrature (exact antiderivatives where the profile
+has one).  The averaged gradient of a cell is the difference of the face (line)
+averages of W divided by the cell size (Gauss formula); a discontinuity lying exactly
+on a face is excluded by taking the one-sided value from inside the cell.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAUSS6_X, GAUSS6_W = np.polynomial.legendre.leggauss(6)
+GAUSS10_X, GAUSS10_W = np.polynomial.legendre.leggauss(10)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based random numbers: splitmix64 (G. Steele, D. Lea, C. Flood,
+# "Fast splittable pseudorandom number generators", OOPSLA 2014).
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def uniform01(seed: int, counter: int) -> float:
+    """U[0,1) from the 53 top bits of splitmix64(seed * 2^32 + counter)."""
+    return (splitmix64(((seed & 0xFFFFFFFF) << 32) + counter) >> 11) * (1.0 / (1 << 53))
+
+
+def uniform01_array(seed: int, n: int) -> np.ndarray:
+    """Vectorised splitmix64 stream: element k = uniform01(seed, k)."""
+    with np.errstate(over="ignore"):
+        x = (np.uint64((seed & 0xFFFFFFFF) << 32) + np.arange(n, dtype=np.uint64))
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+# ---------------------------------------------------------------------------
+# Primitive <-> conservative
+# ---------------------------------------------------------------------------
+def conservative_1d(rho, u, p, gamma):
+    return np.stack([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u])
+
+
+def conservative_2d(rho, u, v, p, gamma):
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+@dataclass
+class State:
+    """Initial state of one problem plus everything needed to run it."""
+    W: np.ndarray
+    Wx: np.ndarray
+    Wy: np.ndarray | None
+    nx: int
+    ny: int
+    gamma: float
+    x0: float
+    x1: float
+    y0: float = 0.0
+    y1: float = 1.0
+    bc_x: int = 0          # 0 periodic, 1 transmissive
+    bc_y: int = 0
+    mu: float = 0.0
+    Pr: float = 1.0
+    order: int = 6
+    recon: int = 0         # 0 linear, 1 WENO-Z
+    t_end: float = 0.0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def dx(self):
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def dy(self):
+        return (self.y1 - self.y0) / self.ny
+
+
+# ---------------------------------------------------------------------------
+# 1D profiles given piecewise: list of (x_left, x_right, f) with f(x) -> (rho, u, p)
+# ---------------------------------------------------------------------------
+def _piece_at(pieces, x, inside_of):
+    """Piece containing x, choosing the one on the side of the cell centre inside_of
+    when x is a breakpoint."""
+    for a, b, f in pieces:
+        if a <= x <= b:
+            if x == a and inside_of < a:
+                continue
+            if x == b and inside_of > b:
+                continue
+            return f
+    raise ValueError(f"x={x} outside profile")
+
+
+def cell_state_1d(pieces, N, x0, x1, gamma):
+    """Exact-to-quadrature cell averages and averaged slopes of conservative variables."""
+    dx = (x1 - x0) / N
+    W = np.zeros((3, 1, N))
+    Wx = np.zeros((3, 1, N))
+    breaks = sorted({a for a, _, _ in pieces} | {b for _, b, _ in pieces})
+    for i in range(N):
+        a, b = x0 + i * dx, x0 + (i + 1) * dx
+        pts = [a] + [q for q in breaks if a < q < b] + [b]
+        acc = np.zeros(3)
+        for lo, hi in zip(pts[:-1], pts[1:]):
+            mid = 0.5 * (lo + hi)
+            f = _piece_at(pieces, mid, mid)
+            xs = mid + 0.5 * (hi - lo) * GAUSS10_X
+            rho, u, p = f(xs)
+            acc += conservative_1d(rho, u, p, gamma) @ GAUSS10_W * 0.5 * (hi - lo)
+        W[:, 0, i] = acc / dx
+        c = 0.5 * (a + b)
+        fr = _piece_at(pieces, b, c)
+        fl = _piece_at(pieces, a, c)
+        wr = conservative_1d(*[np.asarray(q, dtype=float) for q in fr(np.array([b]))], gamma)[:, 0]
+        wl = conservative_1d(*[np.asarray(q, dtype=float) for q in fl(np.array([a]))], gamma)[:, 0]
+        Wx[:, 0, i] = (wr - wl) / dx
+    return W, Wx
+
+
+def density_wave_1d(N: int, t: float = 0.0, gamma: float = 1.4, order: int = 6, recon: int = 0,
+                    x0: float = 0.0, x1: float = 2.0) -> State:
+    """rho = 1 + 0.2 sin(pi (x - t)), U = 1, p = 1 on periodic [0, 2] (Sec. 4.1).
+    Exact averages from the antiderivative."""
+    dx = (x1 - x0) / N
+    xl = x0 + dx * np.arange(N)
+    xr = xl + dx
+    # average of sin(pi (x - t)) over the cell
+    avg_sin = (np.cos(np.pi * (xl - t)) - np.cos(np.pi * (xr - t))) / (np.pi * dx)
+    rho_avg = 1.0 + 0.2 * avg_sin
+    W = np.zeros((3, 1, N))
+    W[0, 0] = rho_avg
+    W[1, 0] = rho_avg                      # U = 1
+    W[2, 0] = 1.0 / (gamma - 1.0) + 0.5 * rho_avg
+    rho_r = 1.0 + 0.2 * np.sin(np.pi * (xr - t))
+    rho_l = 1.0 + 0.2 * np.sin(np.pi * (xl - t))
+    drho = (rho_r - rho_l) / dx
+    Wx = np.zeros((3, 1, N))
+    Wx[0, 0] = drho
+    Wx[1, 0] = drho
+    Wx[2, 0] = 0.5 * drho
+    return State(W, Wx, None, N, 1, gamma, x0, x1, bc_x=0, order=order, recon=recon,
+                 t_end=2.0, name="density_wave_1d")
+
+
+def density_wave_exact_rho(N: int, t: float, x0: float = 0.0, x1: float = 2.0) -> np.ndarray:
+    dx = (x1 - x0) / N
+    xl = x0 + dx * np.arange(N)
+    xr = xl + dx
+    return 1.0 + 0.2 * (np.cos(np.pi * (xl - t)) - np.cos(np.pi * (xr - t))) / (np.pi * dx)
+
+
+def riemann_1d(N: int, left, right, x0: float, x1: float, xjump: float, gamma: float = 1.4,
+               order: int = 8, recon: int = 1, t_end: float = 0.2, name: str = "riemann") -> State:
+    """Piecewise-constant Riemann data (rho, u, p) | (rho, u, p), transmissive ends."""
+    def const(s):
+        return lambda x: tuple(np.full_like(np.asarray(x, dtype=float), q) for q in s)
+    pieces = [(x0, xjump, const(left)), (xjump, x1, const(right))]
+    W, Wx = cell_state_1d(pieces, N, x0, x1, gamma)
+    return State(W, Wx, None, N, 1, gamma, x0, x1, bc_x=1, order=order, recon=recon,
+                 t_end=t_end, name=name, meta=dict(left=tuple(left), right=tuple(right), xjump=xjump))
+
+
+def sod_1d(N: int = 1000, gamma: float = 1.4, order: int = 8, recon: int = 1) -> State:
+    """Sod tube (1, 0, 1) | (0.125, 0, 0.1) on [0, 1], jump at 0.5, t = 0.2."""
+    return riemann_1d(N, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.0, 1.0, 0.5, gamma, order, recon,
+                      0.2, "sod_1d")
+
+
+def shu_osher_1d(N: int = 400, gamma: float = 1.4, order: int = 8, recon: int = 1) -> State:
+    """Shock / density-wave interaction on [-5, 5]: (3.857143, 2.629369, 10.33333) for
+    x < -4, else (1 + 0.2 sin 5x, 0, 1); transmissive ends; t = 1.8."""
+    x0, x1 = -5.0, 5.0
+
+    def left(x):
+        x = np.asarray(x, dtype=float)
+        return np.full_like(x, 3.857143), np.full_like(x, 2.629369), np.full_like(x, 10.33333)
+
+    def right(x):
+        x = np.asarray(x, dtype=float)
+        return 1.0 + 0.2 * np.sin(5.0 * x), np.zeros_like(x), np.ones_like(x)
+
+    W, Wx = cell_state_1d([(x0, -4.0, left), (-4.0, x1, right)], N, x0, x1, gamma)
+    return State(W, Wx, None, N, 1, gamma, x0, x1, bc_x=1, order=order, recon=recon,
+                 t_end=1.8, name="shu_osher_1d")
+
+
+def acoustic_1d(N: int = 40, gamma: float = 1.4, order: int = 8, recon: int = 0) -> State:
+    """Small-amplitude acoustic wave of Sec. 4.3 on periodic [0, 1/3]."""
+    eps, om, rinf, pinf = 1e-5, 6.0 * math.pi, 1.1771, 101325.0
+    ainf = math.sqrt(gamma * pinf / rinf)
+
+    def prof(x):
+        x = np.asarray(x, dtype=float)
+        rho = rinf + eps * rinf * np.cos(2 * om * x)
+        u = eps * ainf * np.cos(om * x)
+        p = pinf * (rho / rinf) ** gamma
+        return rho, u, p
+
+    W, Wx = cell_state_1d([(0.0, 1.0 / 3.0, prof)], N, 0.0, 1.0 / 3.0, gamma)
+    return State(W, Wx, None, N, 1, gamma, 0.0, 1.0 / 3.0, bc_x=0, order=order, recon=recon,
+                 t_end=0.01, name="acoustic_1d")
+
+
+# ---------------------------------------------------------------------------
+# 2D
+# ---------------------------------------------------------------------------
+def _cell_state_2d(point_fn, nx, ny, x0, x1, y0, y1, gamma, rows=None):
+    """Cell averages (6x6 Gauss) and averaged gradients (6-point Gauss on faces) of a smooth
+    point function point_fn(x, y) -> conservative [4, ...]."""
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    xc = x0 + dx * (np.arange(nx) + 0.5)
+    yc = y0 + dy * (np.arange(ny) + 0.5)
+    W = np.zeros((4, ny, nx))
+    Wx = np.zeros((4, ny, nx))
+    Wy = np.zeros((4, ny, nx))
+    gx = 0.5 * GAUSS6_X
+    gw = 0.5 * GAUSS6_W
+    for a in range(6):
+        ys = yc + gx[a] * dy
+        Y = ys[:, None]
+        # face line averages in y at x faces, and the cell average
+        Wx += gw[a] * (point_fn(xc[None, :] + 0.5 * dx, Y) - point_fn(xc[None, :] - 0.5 * dx, Y)) / dx
+        for b in range(6):
+            xs = xc + gx[b] * dx
+            W += gw[a] * gw[b] * point_fn(xs[None, :], Y)
+    for b in range(6):
+        xs = xc + gx[b] * dx
+        X = xs[None, :]
+        Wy += gw[b] * (point_fn(X, yc[:, None] + 0.5 * dy) - point_fn(X, yc[:, None] - 0.5 * dy)) / dy
+    return W, Wx, Wy
+
+
+def vortex_point(x, y, t=0.0, gamma=1.4, beta=5.0, L=10.0, xc=5.0, yc=5.0):
+    """Isentropic vortex of strength beta on the background (1, 1, 1, 1), centre
+    translated by (t, t), nearest periodic image on [0, L]^2."""
+    xb = np.mod(x - xc - t + 0.5 * L, L) - 0.5 * L
+    yb = np.mod(y - yc - t + 0.5 * L, L) - 0.5 * L
+    r2 = xb * xb + yb * yb
+    e = np.exp(0.5 * (1.0 - r2))
+    u = 1.0 - beta / (2 * math.pi) * e * yb
+    v = 1.0 + beta / (2 * math.pi) * e * xb
+    T = 1.0 - (gamma - 1.0) * beta * beta * e * e / (8.0 * gamma * math.pi ** 2)
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return conservative_2d(rho, u, v, p, gamma)
+
+
+def isentropic_vortex_2d(n: int, t: float = 0.0, gamma: float = 1.4, order: int = 8,
+                         recon: int = 0, ny: int | None = None) -> State:
+    ny = n if ny is None else ny
+    W, Wx, Wy = _cell_state_2d(lambda x, y: vortex_point(x, y, t, gamma), n, ny, 0.0, 10.0,
+                               0.0, 10.0 * ny / n, gamma)
+    return State(W, Wx, Wy, n, ny, gamma, 0.0, 10.0, 0.0, 10.0 * ny / n, 0, 0, order=order,
+                 recon=recon, t_end=10.0, name="isentropic_vortex_2d")
+
+
+def vortex_exact_avg(n: int, t: float, gamma: float = 1.4, ny: int | None = None) -> np.ndarray:
+    ny = n if ny is None else ny
+    W, _, _ = _cell_state_2d(lambda x, y: vortex_point(x, y, t, gamma), n, ny, 0.0, 10.0,
+                             0.0, 10.0 * ny / n, gamma)
+    return W
+
+
+def shear_layer_2d(n: int, seed: int = 0, gamma: float = 1.4, mu: float = 1e-4, Pr: float = 0.72,
+                   order: int = 8, recon: int = 1, noise: float = 1e-3) -> State:
+    """Double shear layer on periodic [0,1]^2: rho = 1, p = 1/gamma, u = 0.5 tanh((y-0.25)/0.01)
+    for y <= 0.5 else -0.5 tanh((y-0.75)/0.01), v = 0.01 sin(4 pi x) + noise * U(-1,1) per cell
+    (splitmix64 stream, cell-constant)."""
+    nx = ny = n
+    dx = dy = 1.0 / n
+    nz = noise * (2.0 * uniform01_array(seed, nx * ny).reshape(ny, nx) - 1.0)
+    xc = dx * (np.arange(nx) + 0.5)
+    yc = dy * (np.arange(ny) + 0.5)
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+
+    def pfn_cell(xoff, yoff):
+        x = xc[None, :] + xoff * dx
+        y = yc[:, None] + yoff * dy
+        yy = np.broadcast_to(y, (ny, nx))
+        xx = np.broadcast_to(x, (ny, nx))
+        # piece chosen by the cell centre so that the (smooth) tanh profile is per-cell
+        lower = (yc[:, None] <= 0.5)
+        u = np.where(lower, 0.5 * np.tanh((yy - 0.25) / 0.01), -0.5 * np.tanh((yy - 0.75) / 0.01))
+        v = 0.01 * np.sin(4.0 * math.pi * xx) + nz
+        rho = np.ones_like(u)
+        p = np.full_like(u, 1.0 / gamma)
+        return conservative_2d(rho, u, v, p, gamma)
+
+    gx = 0.5 * GAUSS6_X
+    gw = 0.5 * GAUSS6_W
+    W = np.zeros((4, ny, nx))
+    Wx = np.zeros((4, ny, nx))
+    Wy = np.zeros((4, ny, nx))
+    for a in range(6):
+        Wx += gw[a] * (pfn_cell(0.5, gx[a]) - pfn_cell(-0.5, gx[a])) / dx
+        Wy += gw[a] * (pfn_cell(gx[a], 0.5) - pfn_cell(gx[a], -0.5)) / dy
+        for b in range(6):
+            W += gw[a] * gw[b] * pfn_cell(gx[b], gx[a])
+    del J, I
+    return State(W, Wx, Wy, nx, ny, gamma, 0.0, 1.0, 0.0, 1.0, 0, 0, mu=mu, Pr=Pr, order=order,
+                 recon=recon, t_end=1.0, name="shear_layer_2d")
+
+
+# ---------------------------------------------------------------------------
+# Batched mixed workload: 1D Riemann problems and 2D vortices of uneven sizes.
+# ---------------------------------------------------------------------------
+@dataclass
+class ProblemSpec:
+    kind: str          # "riemann_1d" or "vortex_2d"
+    n: int
+    order: int
+    left: tuple = ()
+    right: tuple = ()
+
+
+def batch_specs(count: int = 512, seed: int = 0, n1_range=(100, 20000), n2_range=(64, 1024)):
+    """Problem s: even -> 1D Riemann, N log-uniform in n1_range, (rho, p) ~ U(0.1, 2) and
+    u ~ U(-1, 1) per side; odd -> 2D vortex, side log-uniform in n2_range; order 6 or 8 from
+    bit 1 of s."""
+    specs = []
+    for s in range(count):
+        base = seed * 1_000_003 + s * 16
+        r = [uniform01(base, k) for k in range(8)]
+        order = 8 if (s >> 1) & 1 else 6
+        if s % 2 == 0:
+            lo, hi = n1_range
+            n = int(round(math.exp(math.log(lo) + r[0] * (math.log(hi) - math.log(lo)))))
+            left = (0.1 + 1.9 * r[1], -1.0 + 2.0 * r[2], 0.1 + 1.9 * r[3])
+            right = (0.1 + 1.9 * r[4], -1.0 + 2.0 * r[5], 0.1 + 1.9 * r[6])
+            specs.append(ProblemSpec("riemann_1d", n, order, left, right))
+        else:
+            lo, hi = n2_range
+            n = int(round(math.exp(math.log(lo) + r[0] * (math.log(hi) - math.log(lo)))))
+            specs.append(ProblemSpec("vortex_2d", n, order))
+    return specs
+
+
+def build_problem(spec: ProblemSpec) -> State:
+    if spec.kind == "riemann_1d":
+        return riemann_1d(spec.n, spec.left, spec.right, 0.0, 1.0, 0.5, 1.4, spec.order, 1, 0.1,
+                          "riemann_1d")
+    return isentropic_vortex_2d(spec.n, 0.0, 1.4, spec.order, 0)
