@@ -1,0 +1,287 @@
+"""Benchmark of the GB300 compact gas-kinetic scheme (one JSON line on rank 0).
+
+Workload: 2D Euler isentropic vortex (strength 5, gamma 1.4) on periodic [0,10]^2, 2048^2
+cells, 8th-order compact linear reconstruction, FP64, fixed dt = CFL 0.3.  A step is one
+full two-stage MSMD step (both face sweeps and both updates, twice).
+Metric: cell-updates/s = cells * steps / seconds (whole job: summed over ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference] [--n 2048]
+
+--impl reference times the FP64 CPU oracle (the plain implementation the tests check the
+GPU against) on the host cores, on bounded windows of the same workload.
+Under torchrun each rank runs an independent replica of the workload (the problems do not
+exchange data): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-updates/s (2D 8th-order GKS, FP64, isentropic vortex)"
+UNIT = "cell-updates/s"
+CFL = 0.3
+# Executed FP64 floating-point operations per face of one face-sweep launch (FMA = 2),
+# from the ncu instruction counters of the sweep (profiles/faces_2d_vortex_fp64.md).
+FLOPS_PER_FACE = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(st, dt, budget_s=12.0, window=128):
+    """The oracle as it stands, on the host cores, on a window of the same workload
+    (transmissive window edges), as many steps as fit in the time budget."""
+    import oracle
+    from paper_1901_00261_gb300 import inputs  # noqa: F401
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    w = min(window, st.nx)
+    sl = (slice(None), slice(0, w), slice(0, w))
+    O = oracle.Solver(w, w, st.gamma, st.mu, st.Pr, st.order, st.recon, 1, 1, 0.0, w * st.dx, 0.0, w * st.dy)
+    O.set_state(np.ascontiguousarray(st.W[sl]), np.ascontiguousarray(st.Wx[sl]),
+                np.ascontiguousarray(st.Wy[sl]))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        O.step(dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    value = w * w * steps / el
+    return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{w}x{w} window of the {st.nx}x{st.ny} workload, {steps} steps, {el:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1901_00261_gb300 import inputs
+    st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
+    import oracle
+    O = oracle.Solver(8, 8)  # builds the library before timing
+    del O
+    # dt of the full workload
+    rho = st.W[0]
+    U, V = st.W[1] / rho, st.W[2] / rho
+    p = 0.4 * (st.W[3] - 0.5 * rho * (U * U + V * V))
+    c = np.sqrt(1.4 * p / rho)
+    dt = CFL / ((np.abs(U) + c) / st.dx + (np.abs(V) + c) / st.dy).max()
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline(st, dt, budget_s=2.0, window=64)
+    for _ in range(args.steps):
+        per_step.append(cpu_baseline(st, dt, budget_s=8.0, window=96))
+    val = statistics.median([r["value"] for r in per_step])
+    cb = dict(per_step[-1])
+    cb["value"] = val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * st.nx * st.ny / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"isentropic_vortex_2d_{args.n}x{args.n}", "cells": args.n * args.n,
+            "order": args.order, "recon": "linear", "precision": "fp64", "cfl": CFL,
+            "domain": "periodic [0,10]^2", "l2_policy": "inputs exceed L2 (state 12 x 8 B per cell)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_1901_00261_gb300 import gks, inputs
+
+    st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
+    stream = torch.cuda.current_stream()
+    G = gks.Solver.from_state(st, stream=stream.cuda_stream)
+    dt = CFL / G.max_wavespeed()
+    ncell = st.nx * st.ny
+    nl = G.launches_per_step()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    G.steps(dt, args.warmup)
+    G.sync()
+    # timed region: K steps with event-bracketed launches on the solver's stream
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        kernel_ms = G.steps_timed(dt, args.steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = t0.elapsed_time(t1)
+    G.sync()
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = ncell * args.steps * ws / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: per step, H2D of the state from
+    # pinned memory, one step, D2H of the resulting state
+    e2e = None
+    if not args.no_e2e:
+        Wp = torch.from_numpy(st.W).pin_memory().numpy()
+        Wxp = torch.from_numpy(st.Wx).pin_memory().numpy()
+        Wyp = torch.from_numpy(st.Wy).pin_memory().numpy()
+        outs = [torch.empty(st.W.shape, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        L = gks.lib()
+        ptr = lambda a: a.ctypes.data_as(gks.ctypes.c_void_p)  # noqa: E731
+        for _ in range(2):
+            G.set_state(Wp, Wxp, Wyp)
+            G.step(dt)
+            L.gks_get_state(G._h, ptr(outs[0]), ptr(outs[1]), ptr(outs[2]))
+        barrier()
+        torch.cuda.synchronize()
+        tw = time.perf_counter()
+        for _ in range(args.steps):
+            G.set_state(Wp, Wxp, Wyp)
+            G.step(dt)
+            rc = L.gks_get_state(G._h, ptr(outs[0]), ptr(outs[1]), ptr(outs[2]))
+            assert rc == 0, gks.last_error()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - tw
+        bytes_state = 3 * st.W.nbytes
+        e2e = {"value": ncell * args.steps * ws / el, "unit": UNIT,
+               "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state}
+
+    # roofline of the dominant kernel (a face sweep), ALU bound against the FP64 FMA probe
+    slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
+                  "x_faces_stage2", "y_faces_stage2", "update_stage2"]
+    per_launch = kernel_ms / args.steps
+    k_dom = int(np.argmax(per_launch))
+    peak64 = gks.probe_alu_peak(True)
+    peak32 = gks.probe_alu_peak(False)
+    name = slot_names[k_dom]
+    nfaces = (st.nx + 1) * st.ny if name.startswith("x") else st.nx * (st.ny + 1)
+    fpf = FLOPS_PER_FACE.get((args.order, name.split("_")[-1]))
+    if fpf is not None and not name.startswith("update"):
+        achieved = fpf * nfaces / (per_launch[k_dom] * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None, "kernel": name,
+                "peak_source": "FP64 FMA-chain probe measured in this run"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": name, "peak_source": "FP64 FMA-chain probe measured in this run"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(args), "e2e": e2e,
+                "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
+                "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)},
+                "alu_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}}
+        if not args.no_cpu and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(st, dt)
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

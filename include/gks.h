@@ -1,0 +1,122 @@
+/* gks.h -- C ABI of the GB300 compact gas-kinetic scheme library (libgks_gb300.so).
+ *
+ * The library advances the compact 6th/8th-order gas-kinetic scheme of Zhao, Ji, Shyy
+ * and Xu (arXiv:1901.00261) on a uniform 1D or 2D grid:
+ *   - per cell it holds the conservative cell averages W = (rho, rho U[, rho V], rho E)
+ *     and their cell-averaged gradients W_x [, W_y] (Sec. 1 and Eq. Gausian-formula);
+ *   - one step is the two-stage fourth-order MSMD update of Eqs. (step-hyper-1) and
+ *     (step-hyper-2), with the interface values updated by the same MSMD (Sec. 2.2);
+ *   - interface fluxes, flux time derivatives and interface values come from the
+ *     time-accurate gas distribution function of Eq. (3rd-simplify-flux) (Sec. 2.1),
+ *     with compact linear reconstruction for the equilibrium part (Sec. 3.1) and compact
+ *     WENO-Z for the initial non-equilibrium part (Sec. 3.3); in 2D, three Gauss points
+ *     per face and a tangential quartic (Sec. 3.1, last paragraph).
+ *
+ * Conventions for every call:
+ *   - Host state arrays are C-contiguous float64 [nvar][ny][nx], nvar = 3 (1D, ny == 1)
+ *     or 4 (2D).  Gradients are dimensional (dW/dx averaged over the cell).
+ *   - The caller owns every buffer it passes; the library owns its device buffers
+ *     (allocated with cudaMalloc on the current device at gks_create, freed by
+ *     gks_destroy).
+ *   - Every int-returning call returns GKS_OK (0) or a negative gks_status; the message
+ *     of the last error on the calling thread is available from gks_last_error().
+ *   - Device work runs on the context's stream (opts.stream, or a stream the library
+ *     creates).  Conditions detected on the device (a non-physical interface state) are
+ *     reported by the next synchronising call (gks_get_state*, gks_sync,
+ *     gks_max_wavespeed) as GKS_ENONPHYSICAL.
+ */
+#ifndef GKS_GB300_H
+#define GKS_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gks_ctx gks_ctx;
+
+typedef enum gks_status {
+  GKS_OK = 0,
+  GKS_EINVAL = -1,         /* invalid argument (sizes, order, gamma, dt, NULL pointer) */
+  GKS_ECUDA = -2,          /* CUDA runtime error (message in gks_last_error) */
+  GKS_ENOMEM = -3,         /* device allocation failed */
+  GKS_ENONPHYSICAL = -4,   /* rho <= 0 or p <= 0 met at an interface point */
+  GKS_ETIMEOUT = -5        /* reserved: a bounded device wait ran out */
+} gks_status;
+
+enum { GKS_RECON_LINEAR = 0, GKS_RECON_WENOZ = 1 };
+enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1 };
+enum { GKS_PREC_FP64 = 0 };
+
+typedef struct gks_opts {
+  double x0, x1, y0, y1;   /* domain; dx = (x1 - x0)/nx, dy = (y1 - y0)/ny */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC or GKS_BC_TRANSMISSIVE (ghost cells copy the
+                              boundary cell's W and gradients) */
+  int precision;           /* GKS_PREC_FP64 */
+  double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-12 */
+  double eps_tau, C_tau;   /* numerical collision time eps*dt + C|pl-pr|/(pl+pr) dt of Sec. 4;
+                              defaults 0.01 and 1 */
+  int use_graph;           /* 1: replay the two-stage step as a captured CUDA graph */
+  void* stream;            /* cudaStream_t to run on; NULL: the library creates one */
+} gks_opts;
+
+/* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-12,
+ * eps_tau 0.01, C_tau 1, use_graph 1, stream NULL. */
+void gks_default_opts(gks_opts* o);
+
+/* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio;
+ * mu >= 0 the dynamic viscosity (0: Euler equations); Pr > 0 the Prandtl number (heat
+ * flux of the Chapman-Enskog terms scaled by 1/Pr); order 6 or 8; recon GKS_RECON_*.
+ * Requires nx >= 5 and (2D) ny >= 5.  opts may be NULL (defaults).  Returns NULL on
+ * error (see gks_last_error). */
+gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int order, int recon,
+                    const gks_opts* opts);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char* gks_last_error(void);
+
+/* Copy a host state into the solver (W, Wx: [nvar][ny][nx]; Wy NULL in 1D). Synchronous. */
+int gks_set_state(gks_ctx* ctx, const double* W, const double* Wx, const double* Wy);
+
+/* Copy the solver state to host arrays; synchronises and reports device conditions. */
+int gks_get_state(gks_ctx* ctx, double* W, double* Wx, double* Wy);
+
+/* Same with device pointers (device-to-device copies, ordered on the context stream;
+ * gks_set_state_device returns without synchronising). */
+int gks_set_state_device(gks_ctx* ctx, const double* W, const double* Wx, const double* Wy);
+int gks_get_state_device(gks_ctx* ctx, double* W, double* Wx, double* Wy);
+
+/* Advance one two-stage MSMD step of size dt > 0 (asynchronous on the context stream). */
+int gks_step(gks_ctx* ctx, double dt);
+
+/* Advance nsteps >= 0 steps of size dt (asynchronous). */
+int gks_steps(gks_ctx* ctx, double dt, int nsteps);
+
+/* max over cells of (|U| + c)/dx (+ (|V| + c)/dy in 2D); dt = CFL / *out.  Synchronises. */
+int gks_max_wavespeed(gks_ctx* ctx, double* out);
+
+/* Wait for the context stream; report device conditions. */
+int gks_sync(gks_ctx* ctx);
+
+/* Device addresses of the state arrays held by the context (valid until gks_destroy). */
+int gks_state_device_ptrs(gks_ctx* ctx, double** W, double** Wx, double** Wy);
+
+/* Number of kernel launches one gks_step issues (for launch accounting). */
+int gks_launches_per_step(gks_ctx* ctx);
+
+/* Measurement helpers (not part of the method).
+ * gks_steps_timed: advance nsteps steps of size dt with plain launches, each bracketed by
+ * CUDA events on the context stream; kernel_ms[k] (k < gks_launches_per_step) receives the
+ * summed duration of launch slot k over the steps (slot order: x-face sweep, [y-face sweep,]
+ * update, for stage 1 then stage 2).  Synchronises.
+ * gks_probe_alu_peak: FLOP/s (FMA = 2) of an FMA-chain kernel over the whole device, in
+ * FP64 (fp64 != 0) or FP32; the denominator of the ALU roofline. */
+int gks_steps_timed(gks_ctx* ctx, double dt, int nsteps, double* kernel_ms);
+int gks_probe_alu_peak(int fp64, double* flops_per_s);
+
+/* Release everything the context owns.  NULL is ignored. */
+void gks_destroy(gks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GKS_GB300_H */

@@ -1,0 +1,557 @@
+// gks_device.cuh -- device arithmetic of the compact 6th/8th-order gas-kinetic scheme
+// (Zhao, Ji, Shyy, Xu, arXiv:1901.00261).  Everything here runs per interface point in
+// the interface's local frame (x = face normal); the kernels in gks_kernels.cu stage
+// the data and call it.
+//
+// R is the bulk arithmetic type (double for the FP64 path, float for the FP32-bulk
+// form); the time-integration coefficients of the exponential terms are always FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace gks {
+
+// ---------------------------------------------------------------------------
+// Compact linear reconstruction (Sec. 3.1): interface value, first and second
+// derivative at x_{i+1/2} from W_{i-1..i+2} and s_k = dx W'_k (printed coefficients of
+// Eqs. recons-6th-val, recons-8th-val, recons-6th-deriva, recons-8th-deriva).
+// ---------------------------------------------------------------------------
+template <typename R, int ORDER>
+__device__ __forceinline__ void linear_recon(R Wm, R W0, R W1, R W2, R sm, R s0, R s1, R s2,
+                                             R& val, R& dh, R& ddh2) {
+  if (ORDER == 6) {
+    val = (Wm + R(299) * (W0 + W1) + W2 - R(3) * (sm - s2) + R(111) * (s0 - s1)) * R(1.0 / 600.0);
+    dh = (R(3411) * (W1 - W0) + R(3) * (W2 - Wm) + R(11) * (sm + s2) - R(941) * (s0 + s1)) * R(1.0 / 1560.0);
+    ddh2 = ((W0 + W1) - (Wm + W2) + R(3) * (sm - s2) + R(51) * (s1 - s0)) * R(1.0 / 40.0);
+  } else {
+    val = (R(25) * (Wm + W2) + R(185) * (W0 + W1) + R(6) * (sm - s2) + R(102) * (s0 - s1)) * R(1.0 / 420.0);
+    dh = (R(270) * (W1 - W0) + R(14) * (W2 - Wm) - R(3) * (sm + s2) - R(99) * (s0 + s1)) * R(1.0 / 108.0);
+    ddh2 = (R(4) * ((W0 + W1) - (Wm + W2)) + (s2 - sm) + R(9) * (s1 - s0)) * R(0.25);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compact WENO-Z left state at x_{i+1/2} (Sec. 3.3 and the Appendix).  Candidates are
+// the Appendix polynomials w(x) = sum A_p (x/dx)^p / p! (A_p = a_p dx^p) about x_i; the
+// w_6 operator before A_4 read as '+'.  beta_1 uses the cubic w~1; the candidate slope
+// of stencil S_1 is that of the quadratic w_1 (= w_3).  The (A_4)^2 constant of the
+// smoothness indicator is the one its definition gives, 87617/80640.
+// Returns the value and dx * derivative.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Cand { R v, d, b; };
+
+template <typename R>
+__device__ __forceinline__ Cand<R> cand_eval(R A0, R A1, R A2, R A3, R A4) {
+  Cand<R> c;
+  c.v = A0 + R(0.5) * A1 + R(0.125) * A2 + R(1.0 / 48.0) * A3 + R(1.0 / 384.0) * A4;
+  c.d = A1 + R(0.5) * A2 + R(0.125) * A3 + R(1.0 / 48.0) * A4;
+  c.b = A1 * A1 + R(13.0 / 12.0) * A2 * A2 + R(1043.0 / 960.0) * A3 * A3 +
+        R(87617.0 / 80640.0) * A4 * A4 + R(1.0 / 12.0) * A1 * A3 + R(7.0 / 80.0) * A2 * A4;
+  return c;
+}
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void weno_left(R Wm, R W0, R W1, R W2, R sm, R s0, R s1, R s2, R eps,
+                                          R& val, R& dh) {
+  const R z = R(0);
+  Cand<R> c0 = cand_eval<R>((Wm + R(11) * W0 + sm) * R(1.0 / 12.0), R(2) * (W0 - Wm) - sm,
+                            R(-2) * (Wm - W0 + sm), z, z);
+  Cand<R> c3 = cand_eval<R>((R(26) * W0 - Wm - W1) * R(1.0 / 24.0), R(0.5) * (W1 - Wm),
+                            Wm - R(2) * W0 + W1, z, z);
+  // w~1: only its smoothness indicator is used
+  R t1 = (R(-23) * Wm + R(20) * W0 + R(3) * W1 - R(10) * sm) * R(1.0 / 16.0);
+  R t2 = Wm - R(2) * W0 + W1;
+  R t3 = R(1.5) * (R(3) * Wm - R(4) * W0 + W1 + R(2) * sm);
+  R b1 = t1 * t1 + R(13.0 / 12.0) * t2 * t2 + R(1043.0 / 960.0) * t3 * t3 + R(1.0 / 12.0) * t1 * t3;
+  Cand<R> c2 = cand_eval<R>((R(43) * W0 + R(16) * W1 - R(11) * W2 + R(6) * s2) * R(1.0 / 48.0),
+                            (R(-31) * W0 + R(60) * W1 - R(29) * W2 + R(14) * s2) * R(1.0 / 16.0),
+                            (R(5) * W0 - R(16) * W1 + R(11) * W2 - R(6) * s2) * R(0.5),
+                            R(1.5) * (R(4) * W1 - W0 - R(3) * W2 + R(2) * s2), z);
+  Cand<R> c4 = cand_eval<R>((R(23) * W0 + R(2) * W1 - W2) * R(1.0 / 24.0),
+                            (R(-3) * W0 + R(4) * W1 - W2) * R(0.5), W0 - R(2) * W1 + W2, z, z);
+  Cand<R> c5 = cand_eval<R>((R(-175) * Wm + R(1148) * W0 - R(13) * W1 - R(54) * sm - R(108) * s0) * R(1.0 / 960.0),
+                            (Wm - W1 + R(10) * s0) * R(0.125),
+                            (R(19) * Wm - R(20) * W0 + W1 + R(6) * sm + R(12) * s0) * R(0.25),
+                            R(-3) * (Wm - W1 + R(2) * s0),
+                            R(-6) * (R(5) * Wm - R(4) * W0 - W1 + R(2) * sm + R(4) * s0));
+  Cand<R> c6 = cand_eval<R>((R(707) * W0 - R(292) * W1 + R(545) * W2 - R(612) * s1 - R(186) * s2) * R(1.0 / 960.0),
+                            (R(-21) * W0 + R(8) * W1 + R(13) * W2 - R(22) * s1 - R(4) * s2) * R(0.125),
+                            (R(25) * W0 + R(28) * W1 - R(53) * W2 + R(60) * s1 + R(18) * s2) * R(0.25),
+                            R(-3) * (R(3) * W0 + R(8) * W1 - R(11) * W2 + R(10) * s1 + R(4) * s2),
+                            R(6) * (W0 + R(4) * W1 - R(5) * W2 + R(4) * s1 + R(2) * s2));
+  // linear weights d^6_k / d^8_k (Sec. 3.3)
+  R d0, d1, d2, d3, d4, d5, d6;
+  if (ORDER == 6) {
+    d0 = R(33.0 / 700); d1 = R(11.0 / 140); d2 = R(22.0 / 175); d3 = R(11.0 / 100);
+    d4 = R(11.0 / 100); d5 = R(37.0 / 140); d6 = R(37.0 / 140);
+  } else {
+    d0 = R(3.0 / 98); d1 = R(5.0 / 98); d2 = R(4.0 / 49); d3 = R(7.0 / 98);
+    d4 = R(7.0 / 98); d5 = R(17.0 / 49); d6 = R(17.0 / 49);
+  }
+  // WENO-Z weights, Eqs. (WENO-Z-w) and (tau)
+  R Z = fabs(R(3) * (c0.b - c4.b) + (c4.b - c3.b));
+  R a0 = d0 * (R(1) + Z / (c0.b + eps));
+  R a1 = d1 * (R(1) + Z / (b1 + eps));
+  R a2 = d2 * (R(1) + Z / (c2.b + eps));
+  R a3 = d3 * (R(1) + Z / (c3.b + eps));
+  R a4 = d4 * (R(1) + Z / (c4.b + eps));
+  R a5 = d5 * (R(1) + Z / (c5.b + eps));
+  R a6 = d6 * (R(1) + Z / (c6.b + eps));
+  R inv = R(1) / (a0 + a1 + a2 + a3 + a4 + a5 + a6);
+  // w_1 and w_3 share point value and slope
+  val = (a0 * c0.v + (a1 + a3) * c3.v + a2 * c2.v + a4 * c4.v + a5 * c5.v + a6 * c6.v) * inv;
+  dh = (a0 * c0.d + (a1 + a3) * c3.d + a2 * c2.d + a4 * c4.d + a5 * c5.d + a6 * c6.d) * inv;
+}
+
+// ---------------------------------------------------------------------------
+// Characteristic projection (Sec. 3.1, characteristic variables) with the Euler
+// eigenvectors of the interface-normal direction at state (rho, U, V, H, c).
+// Right eigenvectors: (1, U-c, V, H-Uc), (1, U, V, q^2/2), (0, 0, 1, V), (1, U+c, V, H+Uc).
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+struct Eig {
+  R U, V, H, c, b1, b2, ic;
+};
+
+template <typename R, int DIM>
+__device__ __forceinline__ Eig<R, DIM> eig_at(const R* W, R gamma) {
+  Eig<R, DIM> e;
+  R irho = R(1) / W[0];
+  e.U = W[1] * irho;
+  e.V = DIM == 2 ? W[2] * irho : R(0);
+  R q2 = e.U * e.U + e.V * e.V;
+  R p = (gamma - R(1)) * (W[DIM + 1] - R(0.5) * W[0] * q2);
+  R c2 = gamma * p * irho;
+  e.c = sqrt(c2);
+  e.ic = R(1) / e.c;
+  e.H = (W[DIM + 1] + p) * irho;
+  e.b1 = (gamma - R(1)) / c2;
+  e.b2 = R(0.5) * q2 * e.b1;
+  return e;
+}
+
+// w = L q (project conservative -> characteristic)
+template <typename R, int DIM>
+__device__ __forceinline__ void eig_left(const Eig<R, DIM>& e, const R* q, R* w) {
+  const int N = DIM + 2;
+  R E = q[N - 1];
+  R mU = e.U * q[1] + (DIM == 2 ? e.V * q[2] : R(0));
+  R base = e.b2 * q[0] - e.b1 * mU + e.b1 * E;   // b2 q0 - b1 (U q1 + V q2) + b1 E
+  R acou = e.ic * (e.U * q[0] - q[1]);
+  w[0] = R(0.5) * (base + acou);
+  w[1] = q[0] - base;
+  if (DIM == 2) w[2] = q[2] - e.V * q[0];
+  w[N - 1] = R(0.5) * (base - acou);
+}
+
+// q = R w (back to conservative)
+template <typename R, int DIM>
+__device__ __forceinline__ void eig_right(const Eig<R, DIM>& e, const R* w, R* q) {
+  const int N = DIM + 2;
+  R wa = w[0], wb = w[1], wd = w[N - 1];
+  R wc = DIM == 2 ? w[2] : R(0);
+  q[0] = wa + wb + wd;
+  q[1] = (e.U - e.c) * wa + e.U * wb + (e.U + e.c) * wd;
+  if (DIM == 2) q[2] = e.V * (wa + wb + wd) + wc;
+  q[N - 1] = (e.H - e.U * e.c) * wa + R(0.5) * (e.U * e.U + e.V * e.V) * wb + (e.H + e.U * e.c) * wd +
+             (DIM == 2 ? e.V * wc : R(0));
+}
+
+// ---------------------------------------------------------------------------
+// Maxwellian and its moments (Sec. 2.1).  g = rho (lam/pi)^{(K+DIM)/2} e^{-lam c^2}.
+// m[k] = <u^k> (full or half space), n[k] = <v^k>, x1 = <xi^2>, x2 = <xi^4>.
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+struct Maxw {
+  R rho, U, V, lam, p;
+  R m[7];
+  R n[7];
+  R x1, x2;
+};
+
+template <typename R, int DIM>
+__device__ __forceinline__ bool maxw_prim(const R* W, R gamma, R K, Maxw<R, DIM>& g) {
+  g.rho = W[0];
+  R irho = R(1) / g.rho;
+  g.U = W[1] * irho;
+  g.V = DIM == 2 ? W[2] * irho : R(0);
+  g.p = (gamma - R(1)) * (W[DIM + 1] - R(0.5) * g.rho * (g.U * g.U + g.V * g.V));
+  g.lam = R(0.5) * g.rho / g.p;
+  R h = R(0.5) / g.lam;   // variance 1/(2 lam)
+  g.x1 = K * h;
+  g.x2 = K * (K + R(2)) * h * h;
+  if (DIM == 2) {
+    g.n[0] = R(1); g.n[1] = g.V;
+#pragma unroll
+    for (int k = 1; k < 6; ++k) g.n[k + 1] = g.V * g.n[k] + R(k) * h * g.n[k - 1];
+  }
+  return (g.rho > R(0)) && (g.p > R(0));
+}
+
+// full-space u moments
+template <typename R, int DIM>
+__device__ __forceinline__ void maxw_full(Maxw<R, DIM>& g) {
+  R h = R(0.5) / g.lam;
+  g.m[0] = R(1); g.m[1] = g.U;
+#pragma unroll
+  for (int k = 1; k < 6; ++k) g.m[k + 1] = g.U * g.m[k] + R(k) * h * g.m[k - 1];
+}
+
+// half-space u moments: sign = +1 for u > 0, -1 for u < 0
+template <typename R, int DIM>
+__device__ __forceinline__ void maxw_half(Maxw<R, DIM>& g, int sign) {
+  R h = R(0.5) / g.lam;
+  R sl = sqrt(g.lam);
+  R s = sign > 0 ? R(1) : R(-1);
+  g.m[0] = R(0.5) * erfc(-s * sl * g.U);
+  g.m[1] = g.U * g.m[0] + s * R(0.5) * exp(-g.lam * g.U * g.U) / (sl * R(1.7724538509055160273));
+#pragma unroll
+  for (int k = 1; k < 6; ++k) g.m[k + 1] = g.U * g.m[k] + R(k) * h * g.m[k - 1];
+}
+
+// Closed-form solution of rho <psi (a.psi)> = b (verified symbolically against the moment
+// matrix of the Maxwellian).
+template <typename R, int DIM>
+__device__ __forceinline__ void maxw_solve(const Maxw<R, DIM>& g, R Kd, const R* b, R* a) {
+  // Kd = K + DIM (internal + translational degrees of freedom)
+  R irho = R(1) / g.rho;   // cheap enough; hoisted by the compiler within a point
+  R il = R(0.5) / g.lam;
+  R Q = g.U * g.U + g.V * g.V + Kd * il;
+  R b1 = b[0] * irho, b2 = b[1] * irho;
+  R R2 = b2 - g.U * b1;
+  R lam2 = R(2) * g.lam;
+  R cK = R(4) * g.lam * g.lam / Kd;
+  if (DIM == 2) {
+    R b3 = b[2] * irho, b4 = b[3] * irho;
+    R R3 = b3 - g.V * b1;
+    R R4 = R(2) * b4 - Q * b1;
+    R a4 = cK * (R4 - R(2) * g.U * R2 - R(2) * g.V * R3);
+    R a3 = lam2 * R3 - g.V * a4;
+    R a2 = lam2 * R2 - g.U * a4;
+    a[0] = b1 - g.U * a2 - g.V * a3 - R(0.5) * a4 * Q;
+    a[1] = a2; a[2] = a3; a[3] = a4;
+  } else {
+    R b3 = b[2] * irho;
+    R R3 = R(2) * b3 - Q * b1;
+    R a3 = cK * (R3 - R(2) * g.U * R2);
+    R a2 = lam2 * R2 - g.U * a3;
+    a[0] = b1 - g.U * a2 - R(0.5) * a3 * Q;
+    a[1] = a2; a[2] = a3;
+  }
+}
+
+// Symmetric moment operator G[k][l] = <psi_k psi_l u^A v^B> over the u-moments in m.
+template <typename R, int DIM>
+struct Gm { R e[DIM == 2 ? 10 : 6]; };
+
+template <typename R, int DIM, int A, int B>
+__device__ __forceinline__ Gm<R, DIM> gmat(const Maxw<R, DIM>& g) {
+  Gm<R, DIM> G;
+  const R* m = g.m;
+  if (DIM == 2) {
+    const R* n = g.n;
+    auto E = [&](int p, int q) { return m[p] * n[q]; };
+    R x1 = g.x1, x2 = g.x2;
+    G.e[0] = E(A, B);                                                             // 00
+    G.e[1] = E(A + 1, B);                                                         // 01
+    G.e[2] = E(A, B + 1);                                                         // 02
+    G.e[3] = R(0.5) * (E(A + 2, B) + E(A, B + 2) + E(A, B) * x1);                 // 03
+    G.e[4] = E(A + 2, B);                                                         // 11
+    G.e[5] = E(A + 1, B + 1);                                                     // 12
+    G.e[6] = R(0.5) * (E(A + 3, B) + E(A + 1, B + 2) + E(A + 1, B) * x1);         // 13
+    G.e[7] = E(A, B + 2);                                                         // 22
+    G.e[8] = R(0.5) * (E(A + 2, B + 1) + E(A, B + 3) + E(A, B + 1) * x1);         // 23
+    G.e[9] = R(0.25) * (E(A + 4, B) + E(A, B + 4) + E(A, B) * x2 +
+                        R(2) * (E(A + 2, B + 2) + (E(A + 2, B) + E(A, B + 2)) * x1));  // 33
+  } else {
+    R x1 = g.x1, x2 = g.x2;
+    G.e[0] = m[A];
+    G.e[1] = m[A + 1];
+    G.e[2] = R(0.5) * (m[A + 2] + m[A] * x1);
+    G.e[3] = m[A + 2];
+    G.e[4] = R(0.5) * (m[A + 3] + m[A + 1] * x1);
+    G.e[5] = R(0.25) * (m[A + 4] + R(2) * m[A + 2] * x1 + m[A] * x2);
+  }
+  return G;
+}
+
+// out = s * G c  (+= if ACC)
+template <typename R, int DIM, bool ACC>
+__device__ __forceinline__ void gmul(const Gm<R, DIM>& G, const R* c, R s, R* out) {
+  if (DIM == 2) {
+    R o0 = G.e[0] * c[0] + G.e[1] * c[1] + G.e[2] * c[2] + G.e[3] * c[3];
+    R o1 = G.e[1] * c[0] + G.e[4] * c[1] + G.e[5] * c[2] + G.e[6] * c[3];
+    R o2 = G.e[2] * c[0] + G.e[5] * c[1] + G.e[7] * c[2] + G.e[8] * c[3];
+    R o3 = G.e[3] * c[0] + G.e[6] * c[1] + G.e[8] * c[2] + G.e[9] * c[3];
+    if (ACC) { out[0] += s * o0; out[1] += s * o1; out[2] += s * o2; out[3] += s * o3; }
+    else { out[0] = s * o0; out[1] = s * o1; out[2] = s * o2; out[3] = s * o3; }
+  } else {
+    R o0 = G.e[0] * c[0] + G.e[1] * c[1] + G.e[2] * c[2];
+    R o1 = G.e[1] * c[0] + G.e[3] * c[1] + G.e[4] * c[2];
+    R o2 = G.e[2] * c[0] + G.e[4] * c[1] + G.e[5] * c[2];
+    if (ACC) { out[0] += s * o0; out[1] += s * o1; out[2] += s * o2; }
+    else { out[0] = s * o0; out[1] = s * o1; out[2] = s * o2; }
+  }
+}
+
+// column 0 of G (moments <psi u^A v^B>)
+template <typename R, int DIM>
+__device__ __forceinline__ void gcol0(const Gm<R, DIM>& G, R s, R* out, bool acc) {
+  if (DIM == 2) {
+    R o[4] = {G.e[0], G.e[1], G.e[2], G.e[3]};
+    for (int k = 0; k < 4; ++k) out[k] = acc ? out[k] + s * o[k] : s * o[k];
+  } else {
+    R o[3] = {G.e[0], G.e[1], G.e[2]};
+    for (int k = 0; k < 3; ++k) out[k] = acc ? out[k] + s * o[k] : s * o[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 time-integration coefficients of the exponential (non-equilibrium) terms.
+// With E0(d) = int_0^d e^{-t/tau} dt, E1(d) = int_0^d t e^{-t/tau} dt and h = dt/2:
+//   a0 = (4 E0(h) - E0(2h))/dt,      a1 = (4 E1(h) - E1(2h))/dt,
+//   b0 = 4 (E0(2h) - 2 E0(h))/dt^2,  b1 = 4 (E1(2h) - 2 E1(h))/dt^2.
+// These are the flux and flux-derivative weights of the linear-in-time fit over
+// [0, dt/2] and [0, dt].  They cancel catastrophically when dt/tau is small, so they are
+// evaluated from stable closed forms (x = h/tau, S = 1 - e^{-x} = -expm1(-x)):
+//   4E0(h)-E0(2h) = tau S (2 + S),  E0(2h)-2E0(h) = -tau S^2,
+// and for the E1 pair by their Taylor series in x when x < 1.
+// ---------------------------------------------------------------------------
+struct TimeCoef { double a0, a1, b0, b1; };
+
+__device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
+  TimeCoef T;
+  double h = 0.5 * dt, x = h / tau;
+  double S = -expm1(-x);
+  double idt = 1.0 / dt;
+  T.a0 = tau * S * (2.0 + S) * idt;
+  T.b0 = -4.0 * tau * S * S * idt * idt;
+  double pa, pb;   // 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x), phi(y) = 1 - e^{-y}(1+y)
+  if (x < 1.0) {
+    // phi(y) = sum_{k>=2} (-1)^k (k-1) y^k / k!
+    double term = x * x * 0.5;   // x^k / k! at k = 2
+    double p2 = 4.0;             // 2^k
+    pa = 0.0; pb = 0.0;
+#pragma unroll
+    for (int k = 2; k < 22; ++k) {
+      double sg = (k & 1) ? -1.0 : 1.0;
+      double ck = sg * (double)(k - 1) * term;
+      pa += ck * (4.0 - p2);
+      pb += ck * (p2 - 2.0);
+      term *= x / (double)(k + 1);
+      p2 *= 2.0;
+    }
+  } else {
+    double e = 1.0 - S;   // e^{-x}
+    double e2 = e * e;
+    pa = 3.0 - 4.0 * e * (1.0 + x) + e2 * (1.0 + 2.0 * x);
+    pb = -1.0 + 2.0 * e * (1.0 + x) - e2 * (1.0 + 2.0 * x);
+  }
+  double t2 = tau * tau;
+  T.a1 = t2 * pa * idt;
+  T.b1 = 4.0 * t2 * pb * idt * idt;
+  return T;
+}
+
+// ---------------------------------------------------------------------------
+// Gas-kinetic evaluation at one interface point (Eq. 3rd-simplify-flux, Sec. 2.2).
+// ---------------------------------------------------------------------------
+struct PhysParams {
+  double gamma, K, mu, Pr, eps_tau, C_tau, weno_eps;
+};
+
+template <typename R, int DIM>
+struct PointIn {
+  R W0[DIM + 2], W0x[DIM + 2], W0xx[DIM + 2];
+  R W0y[DIM + 2], W0xy[DIM + 2], W0yy[DIM + 2];
+  R Wl[DIM + 2], Wlx[DIM + 2], Wly[DIM + 2];
+  R Wr[DIM + 2], Wrx[DIM + 2], Wry[DIM + 2];
+};
+
+template <typename R, int DIM>
+struct PointOut {
+  R F[DIM + 2], Ft[DIM + 2], W0[DIM + 2], Wt[DIM + 2], Wtt[DIM + 2];
+};
+
+// Heat flux q = 1/2 rho <a (a^2 + b^2 + xi^2) P> of P = u (cu.psi) + v (cv.psi) + (c0.psi)
+// over g0, with a = u - U, b = v - V centred Gaussians of variance h = 1/(2 lam).
+// Each c.psi is rewritten about (U, V) as k0 + ka a + kb b + k4/2 C2 (C2 = a^2+b^2+xi^2);
+// only the parts odd in a and even in b survive the average.
+template <typename R, int DIM>
+__device__ __forceinline__ R heat_lin(const Maxw<R, DIM>& g, const R* cu, const R* cv, const R* c0) {
+  R h = R(0.5) / g.lam;
+  R U = g.U, V = DIM == 2 ? g.V : R(0);
+  R bb2 = DIM == 2 ? h : R(0);                 // <b^2>
+  R bb4 = DIM == 2 ? R(3) * h * h : R(0);      // <b^4>
+  R a2 = h, a4 = R(3) * h * h, a6 = R(15) * h * h * h;
+  R xi2 = g.x1, xi4 = g.x2;
+  R Ia2 = a4 + a2 * bb2 + a2 * xi2;                                           // <a^2 C2>
+  R Ia2C4 = a6 + a2 * bb4 + a2 * xi4 + R(2) * (a4 * bb2 + a4 * xi2 + a2 * bb2 * xi2);  // <a^2 C2^2>
+  auto ka_of = [&](const R* c) { return c[1] + c[DIM + 1] * U; };
+  auto k0_of = [&](const R* c) {
+    R c3 = DIM == 2 ? c[2] : R(0);
+    return c[0] + c[1] * U + c3 * V + R(0.5) * c[DIM + 1] * (U * U + V * V);
+  };
+  R q = ka_of(c0) * Ia2;                                          // (c0.psi): ka a
+  q += (U * ka_of(cu) + k0_of(cu)) * Ia2 + R(0.5) * cu[DIM + 1] * Ia2C4;   // (U + a)(cu.psi)
+  if (DIM == 2) q += V * ka_of(cv) * Ia2;                         // (V + b)(cv.psi)
+  return R(0.5) * g.rho * q;
+}
+
+template <typename R, int DIM, bool WENO, bool VISC>
+__device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, DIM>& in, double dt,
+                                          PointOut<R, DIM>& out) {
+  const int N = DIM + 2;
+  const R gamma = R(P.gamma), K = R(P.K), Kd = R(P.K + DIM);
+  bool ok = true;
+  Maxw<R, DIM> g0;
+  R W0c[N];
+  R pl = R(0), pr = R(0);
+  if (WENO) {
+    // Equilibrium value from the collision of the two initial states:
+    // W0 = int_{u>0} psi g_l + int_{u<0} psi g_r.
+    Maxw<R, DIM> gl, gr;
+    ok &= maxw_prim<R, DIM>(in.Wl, gamma, K, gl);
+    ok &= maxw_prim<R, DIM>(in.Wr, gamma, K, gr);
+    maxw_half<R, DIM>(gl, +1);
+    maxw_half<R, DIM>(gr, -1);
+    Gm<R, DIM> Gl = gmat<R, DIM, 0, 0>(gl), Gr = gmat<R, DIM, 0, 0>(gr);
+    gcol0<R, DIM>(Gl, gl.rho, W0c, false);
+    gcol0<R, DIM>(Gr, gr.rho, W0c, true);
+    pl = gl.p; pr = gr.p;
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) W0c[k] = in.W0[k];
+  }
+  ok &= maxw_prim<R, DIM>(W0c, gamma, K, g0);
+  maxw_full<R, DIM>(g0);
+  const R rho0 = g0.rho;
+
+  Gm<R, DIM> G10 = gmat<R, DIM, 1, 0>(g0);
+  Gm<R, DIM> G01;
+  if (DIM == 2) G01 = gmat<R, DIM, 0, 1>(g0);
+
+  // Spatial derivative coefficients (a1, a2) and the compatibility chain (reading R6):
+  // <A> = -<a1 u + a2 v>, <a_xt> = -<a_xx u + a_xy v>, <a_yt> = -<a_xy u + a_yy v>,
+  // <a_tt> = -<a_xt u + a_yt v>.
+  R a1[N], a2[N], Wt[N], A[N];
+  maxw_solve<R, DIM>(g0, Kd, in.W0x, a1);
+  gmul<R, DIM, false>(G10, a1, -rho0, Wt);
+  if (DIM == 2) {
+    maxw_solve<R, DIM>(g0, Kd, in.W0y, a2);
+    gmul<R, DIM, true>(G01, a2, -rho0, Wt);
+  }
+  maxw_solve<R, DIM>(g0, Kd, Wt, A);
+
+  R axt[N], ayt[N], Wtt[N];
+  {
+    R axx[N], bxt[N];
+    maxw_solve<R, DIM>(g0, Kd, in.W0xx, axx);
+    gmul<R, DIM, false>(G10, axx, -rho0, bxt);
+    if (DIM == 2) {
+      R axy[N], ayy[N], byt[N];
+      maxw_solve<R, DIM>(g0, Kd, in.W0xy, axy);
+      maxw_solve<R, DIM>(g0, Kd, in.W0yy, ayy);
+      gmul<R, DIM, true>(G01, axy, -rho0, bxt);
+      gmul<R, DIM, false>(G10, axy, -rho0, byt);
+      gmul<R, DIM, true>(G01, ayy, -rho0, byt);
+      maxw_solve<R, DIM>(g0, Kd, byt, ayt);
+    }
+    maxw_solve<R, DIM>(g0, Kd, bxt, axt);
+  }
+  gmul<R, DIM, false>(G10, axt, -rho0, Wtt);
+  if (DIM == 2) gmul<R, DIM, true>(G01, ayt, -rho0, Wtt);
+
+  // Equilibrium branch: flux and its time derivative at t = 0 (reading R5).
+  R F[N], Ft[N];
+  gcol0<R, DIM>(G10, rho0, F, false);
+  gmul<R, DIM, false>(G10, A, rho0, Ft);
+
+  if (VISC || WENO) {
+    Gm<R, DIM> G20 = gmat<R, DIM, 2, 0>(g0);
+    Gm<R, DIM> G11;
+    if (DIM == 2) G11 = gmat<R, DIM, 1, 1>(g0);
+    if (VISC) {
+      // Chapman-Enskog bracket with the physical collision time mu/p (reading R1).
+      R tau = R(P.mu) / g0.p;
+      R att[N];
+      maxw_solve<R, DIM>(g0, Kd, Wtt, att);
+      R s = -tau * rho0;
+      gmul<R, DIM, true>(G20, a1, s, F);
+      gmul<R, DIM, true>(G10, A, s, F);
+      gmul<R, DIM, true>(G20, axt, s, Ft);
+      gmul<R, DIM, true>(G10, att, s, Ft);
+      if (DIM == 2) {
+        gmul<R, DIM, true>(G11, a2, s, F);
+        gmul<R, DIM, true>(G11, ayt, s, Ft);
+      }
+      if (P.Pr != 1.0) {
+        // Prandtl-number fix (reading R10): (1/Pr - 1) q of the bracket terms.
+        R fpr = R(1.0 / P.Pr - 1.0);
+        R q1 = -tau * heat_lin<R, DIM>(g0, a1, a2, A);
+        R q2 = -tau * heat_lin<R, DIM>(g0, axt, ayt, att);
+        F[N - 1] += fpr * q1;
+        Ft[N - 1] += fpr * q2;
+      }
+    }
+    if (WENO) {
+      // Non-equilibrium branch: -e^{-t/tau} g0 [1 - (a1 u + a2 v) t] + H g_l [...] + (1-H) g_r [...]
+      // time-integrated over [0, dt/2] and [0, dt] and fitted linearly (FP64 coefficients).
+      double p0 = (double)g0.p;
+      double jump = P.C_tau * fabs(((double)pl - (double)pr) / ((double)pl + (double)pr)) * dt;
+      double taun = (P.mu > 0.0 ? P.mu / p0 : P.eps_tau * dt) + jump;
+      TimeCoef T = time_coefs(dt, taun);
+      R c0[N], c1[N];
+      gcol0<R, DIM>(G10, -rho0, c0, false);
+      gmul<R, DIM, false>(G20, a1, rho0, c1);
+      if (DIM == 2) gmul<R, DIM, true>(G11, a2, rho0, c1);
+      {
+        Maxw<R, DIM> gk;
+        R ak1[N], ak2[N];
+        ok &= maxw_prim<R, DIM>(in.Wl, gamma, K, gk);
+        maxw_half<R, DIM>(gk, +1);
+        Gm<R, DIM> H10 = gmat<R, DIM, 1, 0>(gk);
+        gcol0<R, DIM>(H10, gk.rho, c0, true);
+        maxw_solve<R, DIM>(gk, Kd, in.Wlx, ak1);
+        Gm<R, DIM> H20 = gmat<R, DIM, 2, 0>(gk);
+        gmul<R, DIM, true>(H20, ak1, -gk.rho, c1);
+        if (DIM == 2) {
+          maxw_solve<R, DIM>(gk, Kd, in.Wly, ak2);
+          Gm<R, DIM> H11 = gmat<R, DIM, 1, 1>(gk);
+          gmul<R, DIM, true>(H11, ak2, -gk.rho, c1);
+        }
+      }
+      {
+        Maxw<R, DIM> gk;
+        R ak1[N], ak2[N];
+        ok &= maxw_prim<R, DIM>(in.Wr, gamma, K, gk);
+        maxw_half<R, DIM>(gk, -1);
+        Gm<R, DIM> H10 = gmat<R, DIM, 1, 0>(gk);
+        gcol0<R, DIM>(H10, gk.rho, c0, true);
+        maxw_solve<R, DIM>(gk, Kd, in.Wrx, ak1);
+        Gm<R, DIM> H20 = gmat<R, DIM, 2, 0>(gk);
+        gmul<R, DIM, true>(H20, ak1, -gk.rho, c1);
+        if (DIM == 2) {
+          maxw_solve<R, DIM>(gk, Kd, in.Wry, ak2);
+          Gm<R, DIM> H11 = gmat<R, DIM, 1, 1>(gk);
+          gmul<R, DIM, true>(H11, ak2, -gk.rho, c1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        F[k] = R((double)F[k] + T.a0 * (double)c0[k] + T.a1 * (double)c1[k]);
+        Ft[k] = R((double)Ft[k] + T.b0 * (double)c0[k] + T.b1 * (double)c1[k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    out.F[k] = F[k]; out.Ft[k] = Ft[k];
+    out.W0[k] = W0c[k]; out.Wt[k] = Wt[k]; out.Wtt[k] = Wtt[k];
+  }
+  return ok;
+}
+
+}  // namespace gks

@@ -1,0 +1,213 @@
+"""Python binding of the C ABI in include/gks.h (argument marshalling only).
+
+Every step of the scheme runs in the CUDA kernels of libgks_gb300.so; this module only
+loads the library, converts arguments and raises on error codes.  There is no CPU
+fallback: if the library cannot be built or loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GKS_OK, GKS_EINVAL, GKS_ECUDA, GKS_ENOMEM, GKS_ENONPHYSICAL, GKS_ETIMEOUT = 0, -1, -2, -3, -4, -5
+RECON_LINEAR, RECON_WENOZ = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GksError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gks error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("precision", ctypes.c_int),
+                ("weno_eps", ctypes.c_double),
+                ("eps_tau", ctypes.c_double), ("C_tau", ctypes.c_double),
+                ("use_graph", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+# Every symbol include/gks.h declares, with (restype, argtypes).
+_DP = ctypes.POINTER(ctypes.c_double)
+_DPP = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+SIGNATURES = {
+    "gks_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "gks_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]),
+    "gks_last_error": (ctypes.c_char_p, []),
+    "gks_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_set_state_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_get_state_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "gks_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    "gks_max_wavespeed": (ctypes.c_int, [ctypes.c_void_p, _DP]),
+    "gks_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gks_state_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, _DPP, _DPP, _DPP]),
+    "gks_launches_per_step": (ctypes.c_int, [ctypes.c_void_p]),
+    "gks_destroy": (None, [ctypes.c_void_p]),
+    "gks_steps_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _DP]),
+    "gks_probe_alu_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgks_gb300.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgks_gb300.so not found at {path}")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().gks_last_error().decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != GKS_OK:
+        raise GksError(rc, last_error())
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().gks_default_opts(ctypes.byref(o))
+    return o
+
+
+def _host_ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """A gks_ctx: the two-stage compact GKS on an nx x ny grid (ny == 1: 1D).
+
+    Host state arrays are float64 [nvar][ny][nx].  ``stream`` is a CUDA stream handle
+    (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+
+    def __init__(self, nx: int, ny: int = 1, gamma: float = 1.4, mu: float = 0.0, Pr: float = 1.0,
+                 order: int = 6, recon: int = RECON_LINEAR, x0: float = 0.0, x1: float = 1.0,
+                 y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
+                 weno_eps: float = 1e-12, use_graph: bool = True, stream=None):
+        L = lib()
+        o = default_opts()
+        o.x0, o.x1, o.y0, o.y1 = x0, x1, y0, y1
+        o.bc_x, o.bc_y = bc_x, bc_y
+        o.weno_eps = weno_eps
+        o.use_graph = 1 if use_graph else 0
+        o.stream = stream
+        self._h = L.gks_create(nx, ny, gamma, mu, Pr, order, recon, ctypes.byref(o))
+        if not self._h:
+            raise GksError(GKS_EINVAL, last_error())
+        self.nx, self.ny = nx, ny
+        self.dim = 2 if ny > 1 else 1
+        self.nv = self.dim + 2
+
+    @classmethod
+    def from_state(cls, st, **kw):
+        """Solver configured from an inputs.State (grid, BCs, physics, order, recon)."""
+        s = cls(st.nx, st.ny, st.gamma, st.mu, st.Pr, st.order, st.recon, st.x0, st.x1,
+                st.y0, st.y1, st.bc_x, st.bc_y, **kw)
+        s.set_state(st.W, st.Wx, st.Wy)
+        return s
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().gks_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nv, self.ny, self.nx)
+
+    def set_state(self, W, Wx, Wy=None):
+        W = np.ascontiguousarray(W, dtype=np.float64).reshape(self.shape)
+        Wx = np.ascontiguousarray(Wx, dtype=np.float64).reshape(self.shape)
+        Wy = None if self.dim == 1 else np.ascontiguousarray(Wy, dtype=np.float64).reshape(self.shape)
+        _check(lib().gks_set_state(self._h, _host_ptr(W), _host_ptr(Wx), _host_ptr(Wy)))
+
+    def get_state(self):
+        W = np.empty(self.shape)
+        Wx = np.empty(self.shape)
+        Wy = np.empty(self.shape) if self.dim == 2 else None
+        _check(lib().gks_get_state(self._h, _host_ptr(W), _host_ptr(Wx), _host_ptr(Wy)))
+        return W, Wx, Wy
+
+    def set_state_device(self, W_ptr: int, Wx_ptr: int, Wy_ptr: int | None = None):
+        _check(lib().gks_set_state_device(self._h, ctypes.c_void_p(W_ptr), ctypes.c_void_p(Wx_ptr),
+                                          ctypes.c_void_p(Wy_ptr) if Wy_ptr else None))
+
+    def get_state_device(self, W_ptr: int, Wx_ptr: int, Wy_ptr: int | None = None):
+        _check(lib().gks_get_state_device(self._h, ctypes.c_void_p(W_ptr), ctypes.c_void_p(Wx_ptr),
+                                          ctypes.c_void_p(Wy_ptr) if Wy_ptr else None))
+
+    def step(self, dt: float):
+        _check(lib().gks_step(self._h, float(dt)))
+
+    def steps(self, dt: float, n: int):
+        _check(lib().gks_steps(self._h, float(dt), int(n)))
+
+    def max_wavespeed(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().gks_max_wavespeed(self._h, ctypes.byref(v)))
+        return v.value
+
+    def sync(self):
+        _check(lib().gks_sync(self._h))
+
+    def device_ptrs(self):
+        a, b, c = ctypes.POINTER(ctypes.c_double)(), ctypes.POINTER(ctypes.c_double)(), ctypes.POINTER(ctypes.c_double)()
+        _check(lib().gks_state_device_ptrs(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        addr = lambda p: ctypes.cast(p, ctypes.c_void_p).value
+        return addr(a), addr(b), addr(c) if self.dim == 2 else None
+
+    def launches_per_step(self) -> int:
+        return int(lib().gks_launches_per_step(self._h))
+
+    def steps_timed(self, dt: float, n: int) -> np.ndarray:
+        """Run n steps with event-bracketed launches; returns summed ms per launch slot."""
+        ms = np.zeros(self.launches_per_step())
+        _check(lib().gks_steps_timed(self._h, float(dt), int(n),
+                                     ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return ms
+
+
+def probe_alu_peak(fp64: bool = True) -> float:
+    """FLOP/s of an FMA-chain kernel over the whole device (roofline denominator)."""
+    v = ctypes.c_double()
+    _check(lib().gks_probe_alu_peak(1 if fp64 else 0, ctypes.byref(v)))
+    return v.value
