@@ -116,6 +116,28 @@ int gks_probe_alu_peak(int fp64, double* flops_per_s);
 /* Release everything the context owns.  NULL is ignored. */
 void gks_destroy(gks_ctx* ctx);
 
+/* ---- One step without any allocation (the paper has no counterpart) ----
+ * For callers that cannot call cudaMalloc: code inside a memory pool it does not own, a
+ * plug-in whose host forbids device allocation after start-up, or a real-time loop where
+ * an allocation and the synchronisation it may bring are not allowed.  Advances one
+ * two-stage step of the 1D scheme (same kernels as gks_step) from the caller's device
+ * state W, Wx ([3][nx] float64 each) into the caller's device outputs W_out, Wx_out (they
+ * may alias the inputs).  All scratch lives in one static device array of the library
+ * sized for nx <= GKS_STATIC_MAX_NX cells (about 3.1 MB); every GPU that loads the
+ * library holds it until the process exits.  Larger nx is rejected with GKS_EINVAL.
+ * The call allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ * The first call on a device looks up the array's device address on that device; make
+ * that first call before any stream capture.  Every call shares the one array and the
+ * status word it clears at its start: calls that overlap on the GPU (other streams or
+ * threads) race.  Runs on `stream` (NULL: the legacy default stream) and synchronises it
+ * before returning; returns GKS_OK, GKS_EINVAL, GKS_ECUDA or GKS_ENONPHYSICAL, with the
+ * message in gks_static_last_error(). */
+#define GKS_STATIC_MAX_NX 16384
+int gks_step_1d_static(const double* W, const double* Wx, double* W_out, double* Wx_out,
+                       int nx, double gamma, double mu, double Pr, double x0, double x1,
+                       int bc, int order, int recon, double dt, void* stream);
+const char* gks_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

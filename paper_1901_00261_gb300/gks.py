@@ -60,7 +60,13 @@ SIGNATURES = {
     "gks_destroy": (None, [ctypes.c_void_p]),
     "gks_steps_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _DP]),
     "gks_probe_alu_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
+    "gks_step_1d_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
+    "gks_static_last_error": (ctypes.c_char_p, []),
 }
+STATIC_MAX_NX = 16384
 
 
 def library_path() -> str:
