@@ -169,19 +169,25 @@ struct Maxw {
   R m[7];
   R n[7];
   R x1, x2;
+  // constants of the closed-form moment solve
+  R irho, Q, lam2, cK;
 };
 
 template <typename R, int DIM>
 __device__ __forceinline__ bool maxw_prim(const R* W, R gamma, R K, Maxw<R, DIM>& g) {
   g.rho = W[0];
-  R irho = R(1) / g.rho;
+  const R irho = R(1) / g.rho;
   g.U = W[1] * irho;
   g.V = DIM == 2 ? W[2] * irho : R(0);
   g.p = (gamma - R(1)) * (W[DIM + 1] - R(0.5) * g.rho * (g.U * g.U + g.V * g.V));
   g.lam = R(0.5) * g.rho / g.p;
-  R h = R(0.5) / g.lam;   // variance 1/(2 lam)
+  R h = g.p * irho;      // variance 1/(2 lam) = p / rho
   g.x1 = K * h;
   g.x2 = K * (K + R(2)) * h * h;
+  g.irho = irho;
+  g.Q = g.U * g.U + g.V * g.V + (K + R(DIM)) * h;
+  g.lam2 = R(2) * g.lam;
+  g.cK = g.lam2 * g.lam2 / (K + R(DIM));
   if (DIM == 2) {
     g.n[0] = R(1); g.n[1] = g.V;
 #pragma unroll
@@ -193,7 +199,7 @@ __device__ __forceinline__ bool maxw_prim(const R* W, R gamma, R K, Maxw<R, DIM>
 // full-space u moments
 template <typename R, int DIM>
 __device__ __forceinline__ void maxw_full(Maxw<R, DIM>& g) {
-  R h = R(0.5) / g.lam;
+  R h = g.p * g.irho;
   g.m[0] = R(1); g.m[1] = g.U;
 #pragma unroll
   for (int k = 1; k < 6; ++k) g.m[k + 1] = g.U * g.m[k] + R(k) * h * g.m[k - 1];
@@ -202,7 +208,7 @@ __device__ __forceinline__ void maxw_full(Maxw<R, DIM>& g) {
 // half-space u moments: sign = +1 for u > 0, -1 for u < 0
 template <typename R, int DIM>
 __device__ __forceinline__ void maxw_half(Maxw<R, DIM>& g, int sign) {
-  R h = R(0.5) / g.lam;
+  R h = g.p * g.irho;
   R sl = sqrt(g.lam);
   R s = sign > 0 ? R(1) : R(-1);
   g.m[0] = R(0.5) * erfc(-s * sl * g.U);
@@ -214,15 +220,10 @@ __device__ __forceinline__ void maxw_half(Maxw<R, DIM>& g, int sign) {
 // Closed-form solution of rho <psi (a.psi)> = b (verified symbolically against the moment
 // matrix of the Maxwellian).
 template <typename R, int DIM>
-__device__ __forceinline__ void maxw_solve(const Maxw<R, DIM>& g, R Kd, const R* b, R* a) {
-  // Kd = K + DIM (internal + translational degrees of freedom)
-  R irho = R(1) / g.rho;   // cheap enough; hoisted by the compiler within a point
-  R il = R(0.5) / g.lam;
-  R Q = g.U * g.U + g.V * g.V + Kd * il;
+__device__ __forceinline__ void maxw_solve(const Maxw<R, DIM>& g, const R* b, R* a) {
+  const R irho = g.irho, Q = g.Q, lam2 = g.lam2, cK = g.cK;
   R b1 = b[0] * irho, b2 = b[1] * irho;
   R R2 = b2 - g.U * b1;
-  R lam2 = R(2) * g.lam;
-  R cK = R(4) * g.lam * g.lam / Kd;
   if (DIM == 2) {
     R b3 = b[2] * irho, b4 = b[3] * irho;
     R R3 = b3 - g.V * b1;
@@ -400,13 +401,84 @@ __device__ __forceinline__ R heat_lin(const Maxw<R, DIM>& g, const R* cu, const 
   return R(0.5) * g.rho * q;
 }
 
+// ---------------------------------------------------------------------------
+// Euler flux and flux-Jacobian products of the equilibrium state.
+// For a Maxwellian, the perturbations (a.psi) g span the tangent space of the Maxwellian
+// family, so rho<u psi (a.psi)> = A(W) rho<psi (a.psi)> and rho<v psi (a.psi)> = B(W) rho<psi
+// (a.psi)> exactly, with A, B the Jacobians of the Euler fluxes.  The equilibrium branch of
+// Eq. (3rd-simplify-flux) and its compatibility chain are therefore evaluated with A and B
+// (no moments needed).  Local frame: A is the face-normal Jacobian, B the tangential one.
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+struct Flow { R rho, irho, U, V, p, H, g1, q2h; };
+
+template <typename R, int DIM>
+__device__ __forceinline__ Flow<R, DIM> flow_of(const R* W, R gamma) {
+  Flow<R, DIM> f;
+  f.rho = W[0];
+  f.irho = R(1) / f.rho;
+  f.U = W[1] * f.irho;
+  f.V = DIM == 2 ? W[2] * f.irho : R(0);
+  f.q2h = R(0.5) * (f.U * f.U + f.V * f.V);
+  f.g1 = gamma - R(1);
+  f.p = f.g1 * (W[DIM + 1] - f.rho * f.q2h);
+  f.H = (W[DIM + 1] + f.p) * f.irho;
+  return f;
+}
+
+// o = A w (normal Jacobian)
+template <typename R, int DIM>
+__device__ __forceinline__ void jac_n(const Flow<R, DIM>& f, const R* w, R* o) {
+  if (DIM == 2) {
+    R dp = f.g1 * (w[3] - f.U * w[1] - f.V * w[2] + f.q2h * w[0]);
+    R du = w[1] - f.U * w[0];
+    o[0] = w[1];
+    o[1] = f.U * (w[1] + du) + dp;
+    o[2] = f.V * du + f.U * w[2];
+    o[3] = f.U * (w[3] + dp) + f.H * du;
+  } else {
+    R dp = f.g1 * (w[2] - f.U * w[1] + f.q2h * w[0]);
+    R du = w[1] - f.U * w[0];
+    o[0] = w[1];
+    o[1] = f.U * (w[1] + du) + dp;
+    o[2] = f.U * (w[2] + dp) + f.H * du;
+  }
+}
+
+// o = B w (tangential Jacobian, 2D)
+template <typename R>
+__device__ __forceinline__ void jac_t(const Flow<R, 2>& f, const R* w, R* o) {
+  R dp = f.g1 * (w[3] - f.U * w[1] - f.V * w[2] + f.q2h * w[0]);
+  R dv = w[2] - f.V * w[0];
+  o[0] = w[2];
+  o[1] = f.U * dv + f.V * w[1];
+  o[2] = f.V * (w[2] + dv) + dp;
+  o[3] = f.V * (w[3] + dp) + f.H * dv;
+}
+
+// o = -(A x + B y)  (B term only in 2D)
+template <typename R, int DIM>
+__device__ __forceinline__ void neg_div(const Flow<R, DIM>& f, const R* x, const R* y, R* o) {
+  const int N = DIM + 2;
+  R a[N];
+  jac_n<R, DIM>(f, x, a);
+  if (DIM == 2) {
+    R b[4];
+    jac_t<R>(*reinterpret_cast<const Flow<R, 2>*>(&f), y, b);
+#pragma unroll
+    for (int k = 0; k < N; ++k) o[k] = -(a[k] + b[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) o[k] = -a[k];
+  }
+}
+
 template <typename R, int DIM, bool WENO, bool VISC>
 __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, DIM>& in, double dt,
                                           PointOut<R, DIM>& out) {
   const int N = DIM + 2;
-  const R gamma = R(P.gamma), K = R(P.K), Kd = R(P.K + DIM);
+  const R gamma = R(P.gamma), K = R(P.K);
   bool ok = true;
-  Maxw<R, DIM> g0;
   R W0c[N];
   R pl = R(0), pr = R(0);
   if (WENO) {
@@ -425,68 +497,61 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
 #pragma unroll
     for (int k = 0; k < N; ++k) W0c[k] = in.W0[k];
   }
-  ok &= maxw_prim<R, DIM>(W0c, gamma, K, g0);
-  maxw_full<R, DIM>(g0);
-  const R rho0 = g0.rho;
+  const Flow<R, DIM> f = flow_of<R, DIM>(W0c, gamma);
+  ok &= (f.rho > R(0)) && (f.p > R(0));
 
-  Gm<R, DIM> G10 = gmat<R, DIM, 1, 0>(g0);
-  Gm<R, DIM> G01;
-  if (DIM == 2) G01 = gmat<R, DIM, 0, 1>(g0);
-
-  // Spatial derivative coefficients (a1, a2) and the compatibility chain (reading R6):
-  // <A> = -<a1 u + a2 v>, <a_xt> = -<a_xx u + a_xy v>, <a_yt> = -<a_xy u + a_yy v>,
-  // <a_tt> = -<a_xt u + a_yt v>.
-  R a1[N], a2[N], Wt[N], A[N];
-  maxw_solve<R, DIM>(g0, Kd, in.W0x, a1);
-  gmul<R, DIM, false>(G10, a1, -rho0, Wt);
-  if (DIM == 2) {
-    maxw_solve<R, DIM>(g0, Kd, in.W0y, a2);
-    gmul<R, DIM, true>(G01, a2, -rho0, Wt);
-  }
-  maxw_solve<R, DIM>(g0, Kd, Wt, A);
-
-  R axt[N], ayt[N], Wtt[N];
+  // Equilibrium branch at t = 0 (readings R4-R6): F = F_Euler(W0), W_t = -(A W_x + B W_y),
+  // W_xt = -(A W_xx + B W_xy), W_yt = -(A W_xy + B W_yy), W_tt = -(A W_xt + B W_yt), F_t = A W_t.
+  R F[N], Ft[N], Wt[N], Wxt[N], Wyt[N], Wtt[N];
   {
-    R axx[N], bxt[N];
-    maxw_solve<R, DIM>(g0, Kd, in.W0xx, axx);
-    gmul<R, DIM, false>(G10, axx, -rho0, bxt);
-    if (DIM == 2) {
-      R axy[N], ayy[N], byt[N];
-      maxw_solve<R, DIM>(g0, Kd, in.W0xy, axy);
-      maxw_solve<R, DIM>(g0, Kd, in.W0yy, ayy);
-      gmul<R, DIM, true>(G01, axy, -rho0, bxt);
-      gmul<R, DIM, false>(G10, axy, -rho0, byt);
-      gmul<R, DIM, true>(G01, ayy, -rho0, byt);
-      maxw_solve<R, DIM>(g0, Kd, byt, ayt);
-    }
-    maxw_solve<R, DIM>(g0, Kd, bxt, axt);
+    R m = W0c[1];
+    F[0] = m;
+    F[1] = m * f.U + f.p;
+    if (DIM == 2) F[2] = m * f.V;
+    F[N - 1] = f.U * (W0c[N - 1] + f.p);
   }
-  gmul<R, DIM, false>(G10, axt, -rho0, Wtt);
-  if (DIM == 2) gmul<R, DIM, true>(G01, ayt, -rho0, Wtt);
-
-  // Equilibrium branch: flux and its time derivative at t = 0 (reading R5).
-  R F[N], Ft[N];
-  gcol0<R, DIM>(G10, rho0, F, false);
-  gmul<R, DIM, false>(G10, A, rho0, Ft);
+  neg_div<R, DIM>(f, in.W0x, in.W0y, Wt);
+  neg_div<R, DIM>(f, in.W0xx, in.W0xy, Wxt);
+  if (DIM == 2) neg_div<R, DIM>(f, in.W0xy, in.W0yy, Wyt);
+  neg_div<R, DIM>(f, Wxt, Wyt, Wtt);
+  jac_n<R, DIM>(f, Wt, Ft);
 
   if (VISC || WENO) {
+    Maxw<R, DIM> g0;
+    maxw_prim<R, DIM>(W0c, gamma, K, g0);
+    maxw_full<R, DIM>(g0);
+    const R rho0 = g0.rho;
+    R a1[N], a2[N];
+    maxw_solve<R, DIM>(g0, in.W0x, a1);
+    if (DIM == 2) maxw_solve<R, DIM>(g0, in.W0y, a2);
     Gm<R, DIM> G20 = gmat<R, DIM, 2, 0>(g0);
     Gm<R, DIM> G11;
     if (DIM == 2) G11 = gmat<R, DIM, 1, 1>(g0);
     if (VISC) {
-      // Chapman-Enskog bracket with the physical collision time mu/p (reading R1).
+      // Chapman-Enskog bracket with the physical collision time mu/p (reading R1):
+      // -tau rho<u psi (a1 u + a2 v + A)> and -tau rho<u psi (a_xt u + a_yt v + a_tt)>,
+      // where rho<u psi A> = A_n W_t = F_t and rho<u psi a_tt> = A_n W_tt.
       R tau = R(P.mu) / g0.p;
-      R att[N];
-      maxw_solve<R, DIM>(g0, Kd, Wtt, att);
+      R A[N], axt[N], ayt[N], att[N], Fvt[N];
+      maxw_solve<R, DIM>(g0, Wt, A);
+      maxw_solve<R, DIM>(g0, Wxt, axt);
+      maxw_solve<R, DIM>(g0, Wtt, att);
+      if (DIM == 2) maxw_solve<R, DIM>(g0, Wyt, ayt);
+      jac_n<R, DIM>(f, Wtt, Fvt);
       R s = -tau * rho0;
-      gmul<R, DIM, true>(G20, a1, s, F);
-      gmul<R, DIM, true>(G10, A, s, F);
-      gmul<R, DIM, true>(G20, axt, s, Ft);
-      gmul<R, DIM, true>(G10, att, s, Ft);
+      R Fb[N], Fbt[N];
+      gmul<R, DIM, false>(G20, a1, rho0, Fb);
+      gmul<R, DIM, false>(G20, axt, rho0, Fbt);
       if (DIM == 2) {
-        gmul<R, DIM, true>(G11, a2, s, F);
-        gmul<R, DIM, true>(G11, ayt, s, Ft);
+        gmul<R, DIM, true>(G11, a2, rho0, Fb);
+        gmul<R, DIM, true>(G11, ayt, rho0, Fbt);
       }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        F[k] += -tau * (Fb[k] + Ft[k]);
+        Ft[k] += -tau * (Fbt[k] + Fvt[k]);
+      }
+      (void)s;
       if (P.Pr != 1.0) {
         // Prandtl-number fix (reading R10): (1/Pr - 1) q of the bracket terms.
         R fpr = R(1.0 / P.Pr - 1.0);
@@ -499,42 +564,36 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
     if (WENO) {
       // Non-equilibrium branch: -e^{-t/tau} g0 [1 - (a1 u + a2 v) t] + H g_l [...] + (1-H) g_r [...]
       // time-integrated over [0, dt/2] and [0, dt] and fitted linearly (FP64 coefficients).
+      // rho0 <u psi> = F_Euler(W0).
       double p0 = (double)g0.p;
       double jump = P.C_tau * fabs(((double)pl - (double)pr) / ((double)pl + (double)pr)) * dt;
       double taun = (P.mu > 0.0 ? P.mu / p0 : P.eps_tau * dt) + jump;
       TimeCoef T = time_coefs(dt, taun);
       R c0[N], c1[N];
-      gcol0<R, DIM>(G10, -rho0, c0, false);
+#pragma unroll
+      for (int k = 0; k < N; ++k) c0[k] = -F[k];
+      if (VISC) {
+        // c0 needs the collisionless flux of g0 only (the bracket is not part of it)
+        R m = W0c[1];
+        c0[0] = -m; c0[1] = -(m * f.U + f.p);
+        if (DIM == 2) c0[2] = -m * f.V;
+        c0[N - 1] = -f.U * (W0c[N - 1] + f.p);
+      }
       gmul<R, DIM, false>(G20, a1, rho0, c1);
       if (DIM == 2) gmul<R, DIM, true>(G11, a2, rho0, c1);
-      {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
         Maxw<R, DIM> gk;
         R ak1[N], ak2[N];
-        ok &= maxw_prim<R, DIM>(in.Wl, gamma, K, gk);
-        maxw_half<R, DIM>(gk, +1);
+        ok &= maxw_prim<R, DIM>(side == 0 ? in.Wl : in.Wr, gamma, K, gk);
+        maxw_half<R, DIM>(gk, side == 0 ? +1 : -1);
         Gm<R, DIM> H10 = gmat<R, DIM, 1, 0>(gk);
         gcol0<R, DIM>(H10, gk.rho, c0, true);
-        maxw_solve<R, DIM>(gk, Kd, in.Wlx, ak1);
+        maxw_solve<R, DIM>(gk, side == 0 ? in.Wlx : in.Wrx, ak1);
         Gm<R, DIM> H20 = gmat<R, DIM, 2, 0>(gk);
         gmul<R, DIM, true>(H20, ak1, -gk.rho, c1);
         if (DIM == 2) {
-          maxw_solve<R, DIM>(gk, Kd, in.Wly, ak2);
-          Gm<R, DIM> H11 = gmat<R, DIM, 1, 1>(gk);
-          gmul<R, DIM, true>(H11, ak2, -gk.rho, c1);
-        }
-      }
-      {
-        Maxw<R, DIM> gk;
-        R ak1[N], ak2[N];
-        ok &= maxw_prim<R, DIM>(in.Wr, gamma, K, gk);
-        maxw_half<R, DIM>(gk, -1);
-        Gm<R, DIM> H10 = gmat<R, DIM, 1, 0>(gk);
-        gcol0<R, DIM>(H10, gk.rho, c0, true);
-        maxw_solve<R, DIM>(gk, Kd, in.Wrx, ak1);
-        Gm<R, DIM> H20 = gmat<R, DIM, 2, 0>(gk);
-        gmul<R, DIM, true>(H20, ak1, -gk.rho, c1);
-        if (DIM == 2) {
-          maxw_solve<R, DIM>(gk, Kd, in.Wry, ak2);
+          maxw_solve<R, DIM>(gk, side == 0 ? in.Wly : in.Wry, ak2);
           Gm<R, DIM> H11 = gmat<R, DIM, 1, 1>(gk);
           gmul<R, DIM, true>(H11, ak2, -gk.rho, c1);
         }
