@@ -1,8 +1,10 @@
 """Benchmark of the GB300 compact gas-kinetic scheme (one JSON line on rank 0).
 
 Workload: 2D Euler isentropic vortex (strength 5, gamma 1.4) on periodic [0,10]^2, 2048^2
-cells, 8th-order compact linear reconstruction, FP64, fixed dt = CFL 0.3.  A step is one
-full two-stage MSMD step (both face sweeps and both updates, twice).
+cells, 8th-order compact linear reconstruction, fixed dt = CFL 0.3.  A step is one full
+two-stage MSMD step (both face sweeps and both updates, twice).  Both forms run on the same
+input: the FP32-bulk form (the headline value) and the plain FP64 form; each reports its
+L1 density error against the exact (translated) solution at the end of its run.
 Metric: cell-updates/s = cells * steps / seconds (whole job: summed over ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference] [--n 2048]
@@ -28,13 +30,15 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "cell-updates/s (2D 8th-order GKS, FP64, isentropic vortex)"
+METRIC = "cell-updates/s (2D 8th-order GKS, FP32-bulk vs FP64, isentropic vortex)"
 UNIT = "cell-updates/s"
 CFL = 0.3
 # FP64 floating-point operations per face of one face-sweep launch (FMA = 2) of the 2D
 # 8th-order linear Euler sweep, counted by ncu's executed-instruction counters
 # (768.6 DFMA + 243.0 DMUL + 130.0 DADD per face; profiles/faces_2d_vortex_fp64.md).
-FLOPS_PER_FACE = {(8, "stage1"): 1910.2, (8, "stage2"): 1910.2}
+FLOPS_PER_FACE = {("fp64", 8): 1910.2,
+                  # FP32-bulk sweep (x faces, stage 1): 807.2 FFMA + 282.0 FMUL + 326.1 FADD per face
+                  ("fp32", 8): 2222.5}
 
 
 def parse():
@@ -47,6 +51,8 @@ def parse():
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-acc", action="store_true", help="skip the L1 error against the exact solution")
+    ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
     return ap.parse_args()
 
 
@@ -167,7 +173,7 @@ def run_reference(args, ws, rank):
 
 def workload_config(args):
     return {"workload": f"isentropic_vortex_2d_{args.n}x{args.n}", "cells": args.n * args.n,
-            "order": args.order, "recon": "linear", "precision": "fp64", "cfl": CFL,
+            "order": args.order, "recon": "linear", "precision": "fp32-bulk (headline) and fp64", "cfl": CFL,
             "domain": "periodic [0,10]^2", "l2_policy": "inputs exceed L2 (state 12 x 8 B per cell)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -190,37 +196,68 @@ def main():
 
     st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
     stream = torch.cuda.current_stream()
-    G = gks.Solver.from_state(st, stream=stream.cuda_stream)
-    dt = CFL / G.max_wavespeed()
     ncell = st.nx * st.ny
-    nl = G.launches_per_step()
+    slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
+                  "x_faces_stage2", "y_faces_stage2", "update_stage2"]
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # warm-up
-    G.steps(dt, args.warmup)
-    G.sync()
-    # timed region: K steps with event-bracketed launches on the solver's stream
-    barrier()
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        t0.record(stream)
-        kernel_ms = G.steps_timed(dt, args.steps)
-        t1.record(stream)
+    peak64 = gks.probe_alu_peak(True)
+    peak32 = gks.probe_alu_peak(False)
+    forms = {"both": ["fp32", "fp64"], "fp32": ["fp32"], "fp64": ["fp64"]}[args.precision]
+    results = {}
+    for form in forms:
+        prec = gks.PREC_FP32_BULK if form == "fp32" else gks.PREC_FP64
+        G = gks.Solver.from_state(st, stream=stream.cuda_stream, precision=prec)
+        dt = CFL / G.max_wavespeed()
+        nl = G.launches_per_step()
+        G.steps(dt, args.warmup)
+        G.sync()
+        barrier()
         torch.cuda.synchronize()
-    barrier()
-    ms = t0.elapsed_time(t1)
-    G.sync()
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ncell * args.steps * ws / (ms * 1e-3)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            t0.record(stream)
+            kernel_ms = G.steps_timed(dt, args.steps)
+            t1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = t0.elapsed_time(t1)
+        G.sync()
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        per_launch = kernel_ms / args.steps
+        k_dom = int(np.argmax(per_launch))
+        name = slot_names[k_dom]
+        nfaces = (st.nx + 1) * st.ny if name.startswith("x") else st.nx * (st.ny + 1)
+        fpf = FLOPS_PER_FACE.get((form, args.order))
+        peak = peak64 if form == "fp64" else peak32
+        roof = {"bound": "alu", "achieved": None, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": name,
+                "peak_source": f"{'FP64' if form == 'fp64' else 'FP32'} FMA-chain probe measured in this run"}
+        if fpf is not None and not name.startswith("update"):
+            achieved = fpf * nfaces / (per_launch[k_dom] * 1e-3)
+            roof.update(achieved=achieved / 1e12, frac=achieved / peak)
+        r = {"value": ncell * args.steps * ws / (ms * 1e-3), "ms_per_step": ms / args.steps,
+             "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
+             "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}
+        if not args.no_acc and rank == 0:
+            T = dt * (args.warmup + args.steps)
+            W, _, _ = G.get_state()
+            ex = inputs.vortex_exact_avg(args.n, T)
+            r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
+            r["t_end"] = T
+            results.setdefault("_W", {})[form] = W[0]
+        results[form] = r
+        results.setdefault("_solver", {})[form] = (G, dt)
 
+    head = forms[0]
+    G, dt = results["_solver"][head]
     # end to end through the public API with host buffers: per step, H2D of the state from
     # pinned memory, one step, D2H of the resulting state
     e2e = None
@@ -249,37 +286,28 @@ def main():
         e2e = {"value": ncell * args.steps * ws / el, "unit": UNIT,
                "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state}
 
-    # roofline of the dominant kernel (a face sweep), ALU bound against the FP64 FMA probe
-    slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
-                  "x_faces_stage2", "y_faces_stage2", "update_stage2"]
-    per_launch = kernel_ms / args.steps
-    k_dom = int(np.argmax(per_launch))
-    peak64 = gks.probe_alu_peak(True)
-    peak32 = gks.probe_alu_peak(False)
-    name = slot_names[k_dom]
-    nfaces = (st.nx + 1) * st.ny if name.startswith("x") else st.nx * (st.ny + 1)
-    fpf = FLOPS_PER_FACE.get((args.order, name.split("_")[-1]))
-    if fpf is not None and not name.startswith("update"):
-        achieved = fpf * nfaces / (per_launch[k_dom] * 1e-3)
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": None, "kernel": name,
-                "peak_source": "FP64 FMA-chain probe measured in this run"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": name, "peak_source": "FP64 FMA-chain probe measured in this run"}
-
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(args), "e2e": e2e,
-                "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
-                "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)},
+        h = results[head]
+        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32-bulk (f64 time coefficients and accumulation)" if head == "fp32" else "f64",
+                "data": "synthetic", "config": workload_config(args), "e2e": e2e,
+                "gpu_launches": h["gpu_launches"], "roofline": h["roofline"], "clocks": h["clocks"],
+                "kernel_ms_per_launch": h["kernel_ms_per_launch"],
                 "alu_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}}
+        for form in forms:
+            r = results[form]
+            line[form] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "l1_rho_vs_exact", "t_end",
+                                            "kernel_ms_per_launch") if k in r}
+        if "_W" in results and len(results["_W"]) == 2:
+            a, b = results["_W"]["fp32"], results["_W"]["fp64"]
+            line["fp32_vs_fp64_l1_rho"] = float(np.abs(a - b).mean())
         if not args.no_cpu and ws == 1:
             line["cpu_baseline"] = cpu_baseline(st, dt)
         print(json.dumps(line), flush=True)
-    G.close()
+    for form in forms:
+        results["_solver"][form][0].close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -45,13 +45,18 @@ typedef enum gks_status {
 
 enum { GKS_RECON_LINEAR = 0, GKS_RECON_WENOZ = 1 };
 enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1 };
-enum { GKS_PREC_FP64 = 0 };
+/* GKS_PREC_FP64: every step in FP64.
+ * GKS_PREC_FP32_BULK: reconstruction, WENO-Z and gas-kinetic arithmetic of the face sweeps in
+ * FP32 on differences from a reference cell (the state mirrored as float hi/lo pairs); the
+ * time-integration coefficients of the exponential terms and the MSMD accumulation of cell
+ * averages and slopes in FP64 (conservation is exact). */
+enum { GKS_PREC_FP64 = 0, GKS_PREC_FP32_BULK = 1 };
 
 typedef struct gks_opts {
   double x0, x1, y0, y1;   /* domain; dx = (x1 - x0)/nx, dy = (y1 - y0)/ny */
   int bc_x, bc_y;          /* GKS_BC_PERIODIC or GKS_BC_TRANSMISSIVE (ghost cells copy the
                               boundary cell's W and gradients) */
-  int precision;           /* GKS_PREC_FP64 */
+  int precision;           /* GKS_PREC_FP64 or GKS_PREC_FP32_BULK */
   double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-12 */
   double eps_tau, C_tau;   /* numerical collision time eps*dt + C|pl-pr|/(pl+pr) dt of Sec. 4;
                               defaults 0.01 and 1 */

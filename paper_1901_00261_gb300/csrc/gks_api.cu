@@ -44,6 +44,8 @@ struct gks_ctx {
   double* fx = nullptr;      // x-face buffer [4][nv][ny][nx+1]
   double* fy = nullptr;      // y-face buffer [4][nv][ny+1][nx]
   double* d_dt = nullptr;
+  float* mirror = nullptr;   // FP32-bulk: [hi | lo | Wx | Wy] floats
+  double* fref = nullptr;    // FP32-bulk: per-cell Euler fluxes [F | G] of the state
   unsigned int* d_status = nullptr;
   unsigned long long* d_ws = nullptr;
   double last_dt = -1.0;
@@ -64,6 +66,47 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     if (!begin) ++slot;
   };
   cudaError_t e;
+  if (c->o.precision == GKS_PREC_FP32_BULK) {
+    const long L = state_len(c);
+    gks::FaceArgs32 fa;
+    fa.dtp = c->d_dt; fa.status = c->d_status;
+    fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
+    fa.P = c->P;
+    fa.M = c->mirror;
+    fa.fref = c->fref;
+    fa.dnf = (float)c->dx; fa.gammaf = (float)c->P.gamma; fa.epsf = (float)c->P.weno_eps;
+    const bool visc = c->P.mu > 0.0;
+    gks::UpdateArgs32 ua;
+    ua.fx = reinterpret_cast<const float*>(c->fx); ua.fy = reinterpret_cast<const float*>(c->fy);
+    ua.acc = c->acc; ua.M = c->mirror; ua.fref = c->fref; ua.dtp = c->d_dt;
+    ua.nx = c->nx; ua.ny = c->ny; ua.bcx = c->o.bc_x; ua.bcy = c->o.bc_y;
+    ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy; ua.gamma = c->P.gamma;
+    for (int stage = 1; stage <= 2; ++stage) {
+      fa.stage = stage;
+      fa.Mn = c->mirror + 2 * L; fa.out = c->fx; fa.dn = c->dx; fa.dtan = c->dy;
+      fa.dnf = (float)c->dx; fa.itanf = (float)(1.0 / c->dy);
+      mark(true);
+      if (c->dim == 1) e = gks::launch_faces32_1d(fa, c->order, c->recon, visc, c->stream);
+      else e = gks::launch_faces32_2d(fa, 0, c->order, c->recon, visc, c->stream);
+      mark(false);
+      if (e != cudaSuccess) return cuda_fail(e, "x-face sweep (fp32)");
+      if (c->dim == 2) {
+        fa.Mn = c->mirror + 3 * L; fa.out = c->fy; fa.dn = c->dy; fa.dtan = c->dx;
+        fa.dnf = (float)c->dy; fa.itanf = (float)(1.0 / c->dx);
+        mark(true);
+        e = gks::launch_faces32_2d(fa, 1, c->order, c->recon, visc, c->stream);
+        mark(false);
+        if (e != cudaSuccess) return cuda_fail(e, "y-face sweep (fp32)");
+      }
+      ua.W = c->state;
+      ua.Ws = c->state;   // written by stage 2 only
+      mark(true);
+      e = gks::launch_update32(ua, c->dim, stage, c->stream);
+      mark(false);
+      if (e != cudaSuccess) return cuda_fail(e, "cell update (fp32)");
+    }
+    return GKS_OK;
+  }
   gks::FaceArgs fa;
   fa.dtp = c->d_dt; fa.status = c->d_status;
   fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
@@ -98,6 +141,14 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     mark(false);
     if (e != cudaSuccess) return cuda_fail(e, "cell update");
   }
+  return GKS_OK;
+}
+
+// FP32-bulk: rebuild the float mirror after the FP64 state was replaced.
+int refresh_mirror(gks_ctx* c) {
+  if (c->o.precision != GKS_PREC_FP32_BULK) return GKS_OK;
+  cudaError_t e = gks::launch_mirror_ref(c->state, c->mirror, c->fref, c->nx, c->ny, c->dim, c->P.gamma, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mirror");
   return GKS_OK;
 }
 
@@ -142,7 +193,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   if (opts) o = *opts; else gks_default_opts(&o);
   if (!(o.x1 > o.x0) || (ny > 1 && !(o.y1 > o.y0))) { fail(GKS_EINVAL, "empty domain%s"); return nullptr; }
   if ((o.bc_x != 0 && o.bc_x != 1) || (o.bc_y != 0 && o.bc_y != 1)) { fail(GKS_EINVAL, "bc must be 0 or 1%s"); return nullptr; }
-  if (o.precision != GKS_PREC_FP64) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
+  if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_FP32_BULK) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
 
   gks_ctx* c = new (std::nothrow) gks_ctx();
@@ -176,6 +227,11 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
     e = cudaMalloc((void**)b.p, b.n * sizeof(double));
     if (e != cudaSuccess) { cuda_fail(e, "device allocation"); gks_destroy(c); return nullptr; }
   }
+  if (o.precision == GKS_PREC_FP32_BULK) {
+    e = cudaMalloc((void**)&c->mirror, (size_t)(c->dim + 2) * L * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fref, (size_t)c->dim * L * sizeof(double));
+    if (e != cudaSuccess) { cuda_fail(e, "device allocation"); gks_destroy(c); return nullptr; }
+  }
   e = cudaMalloc((void**)&c->d_status, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ws, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
@@ -193,6 +249,8 @@ int gks_set_state(gks_ctx* c, const double* W, const double* Wx, const double* W
     cudaError_t e = cudaMemcpyAsync(c->state + k * L, src[k], L * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
   }
+  int rc = refresh_mirror(c);
+  if (rc != GKS_OK) return rc;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_state");
   return GKS_OK;
@@ -206,7 +264,7 @@ int gks_set_state_device(gks_ctx* c, const double* W, const double* Wx, const do
     cudaError_t e = cudaMemcpyAsync(c->state + k * L, src[k], L * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set_state_device copy");
   }
-  return GKS_OK;
+  return refresh_mirror(c);
 }
 
 int gks_get_state(gks_ctx* c, double* W, double* Wx, double* Wy) {
@@ -349,6 +407,8 @@ void gks_destroy(gks_ctx* c) {
   double* bufs[] = {c->state, c->stage, c->acc, c->fx, c->fy, c->d_dt};
   for (double* b : bufs) if (b) cudaFree(b);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->mirror) cudaFree(c->mirror);
+  if (c->fref) cudaFree(c->fref);
   if (c->d_ws) cudaFree(c->d_ws);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -473,9 +473,36 @@ __device__ __forceinline__ void neg_div(const Flow<R, DIM>& f, const R* x, const
   }
 }
 
-template <typename R, int DIM, bool WENO, bool VISC>
+// Change of the Euler flux (normal direction) between the reference state r and r + d,
+// F(r + d) - F(r), written so that every term is a product with a component of d: in
+// single precision its error is relative to the change, not to the flux.
+template <typename R, int DIM>
+__device__ __forceinline__ void euler_flux_delta(const R* r, const R* d, R gamma, R* o) {
+  const int N = DIM + 2;
+  R rho = r[0], m = r[1], n = DIM == 2 ? r[2] : R(0), E = r[N - 1];
+  R drho = d[0], dm = d[1], dn = DIM == 2 ? d[2] : R(0), dE = d[N - 1];
+  R irho = R(1) / rho;
+  R q = irho / (rho + drho);                             // 1 / (rho (rho + drho))
+  R U = m * irho, V = n * irho;
+  R dmm = (rho * dm * (R(2) * m + dm) - m * m * drho) * q;    // d(m^2/rho)
+  R dnn = (rho * dn * (R(2) * n + dn) - n * n * drho) * q;    // d(n^2/rho)
+  R dU = (rho * dm - m * drho) * q;                           // d(m/rho)
+  R p = (gamma - R(1)) * (E - R(0.5) * (m * U + n * V));
+  R dp = (gamma - R(1)) * (dE - R(0.5) * (dmm + dnn));
+  o[0] = dm;
+  o[1] = dmm + dp;
+  if (DIM == 2) o[2] = (rho * (m * dn + n * dm + dm * dn) - m * n * drho) * q;   // d(mn/rho)
+  o[N - 1] = (E + p) * dU + (dE + dp) * (U + dU);
+}
+
+// DELTA: single-precision form.  in.W0, in.Wl, in.Wr hold full states ref + delta (used by
+// the nonlinear functions), d0 the delta of the linear reconstruction value; out.F is then
+// F - F_Euler(ref) and out.W0 is W0 - ref (the FP64 reference parts are added in the cell
+// update).
+template <typename R, int DIM, bool WENO, bool VISC, bool DELTA = false>
 __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, DIM>& in, double dt,
-                                          PointOut<R, DIM>& out) {
+                                          PointOut<R, DIM>& out, const R* ref = nullptr,
+                                          const R* d0 = nullptr) {
   const int N = DIM + 2;
   const R gamma = R(P.gamma), K = R(P.K);
   bool ok = true;
@@ -503,7 +530,12 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
   // Equilibrium branch at t = 0 (readings R4-R6): F = F_Euler(W0), W_t = -(A W_x + B W_y),
   // W_xt = -(A W_xx + B W_xy), W_yt = -(A W_xy + B W_yy), W_tt = -(A W_xt + B W_yt), F_t = A W_t.
   R F[N], Ft[N], Wt[N], Wxt[N], Wyt[N], Wtt[N];
-  {
+  R dW0[N];   // W0 - ref in the DELTA form
+  if (DELTA) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) dW0[k] = WENO ? W0c[k] - ref[k] : d0[k];
+    euler_flux_delta<R, DIM>(ref, dW0, gamma, F);
+  } else {
     R m = W0c[1];
     F[0] = m;
     F[1] = m * f.U + f.p;
@@ -572,7 +604,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       R c0[N], c1[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) c0[k] = -F[k];
-      if (VISC) {
+      if (VISC || DELTA) {
         // c0 needs the collisionless flux of g0 only (the bracket is not part of it)
         R m = W0c[1];
         c0[0] = -m; c0[1] = -(m * f.U + f.p);
@@ -608,7 +640,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     out.F[k] = F[k]; out.Ft[k] = Ft[k];
-    out.W0[k] = W0c[k]; out.Wt[k] = Wt[k]; out.Wtt[k] = Wtt[k];
+    out.W0[k] = DELTA ? dW0[k] : W0c[k]; out.Wt[k] = Wt[k]; out.Wtt[k] = Wtt[k];
   }
   return ok;
 }

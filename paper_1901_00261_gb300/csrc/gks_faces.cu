@@ -15,99 +15,9 @@
 // Face buffer layouts: x faces [comp][v][ny][nx+1] (face f at x_{f-1/2}); y faces
 // [comp][v][ny+1][nx].
 #include "gks_kernels.cuh"
+#include "gks_sweep.cuh"
 
 namespace gks {
-
-__device__ __forceinline__ int map_index(int i, int n, int bc) {
-  if (bc == 0) { i %= n; return i < 0 ? i + n : i; }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
-}
-
-// Tangential quartic through the averages over the five unit segments centred at -2..2:
-// weights of the value, d/ds and d2/ds2 at the Gauss points s = -sqrt(3/5)/2, 0, +sqrt(3/5)/2.
-#define GKS_SQ15 3.87298334620741688518
-__device__ __constant__ double TW[3][3][5] = {
-    {{-11.0 * GKS_SQ15 / 1200 - 3.0 / 800, 29.0 / 600 + 41.0 * GKS_SQ15 / 600, 1093.0 / 1200,
-      29.0 / 600 - 41.0 * GKS_SQ15 / 600, -3.0 / 800 + 11.0 * GKS_SQ15 / 1200},
-     {GKS_SQ15 / 100 + 1.0 / 15, -19.0 / 30 - 7.0 * GKS_SQ15 / 50, 13.0 * GKS_SQ15 / 50,
-      19.0 / 30 - 7.0 * GKS_SQ15 / 50, -1.0 / 15 + GKS_SQ15 / 100},
-     {-1.0 / 20 + GKS_SQ15 / 20, 6.0 / 5 - GKS_SQ15 / 10, -23.0 / 10, GKS_SQ15 / 10 + 6.0 / 5,
-      -GKS_SQ15 / 20 - 1.0 / 20}},
-    {{3.0 / 640, -29.0 / 480, 1067.0 / 960, -29.0 / 480, 3.0 / 640},
-     {5.0 / 48, -17.0 / 24, 0.0, 17.0 / 24, -5.0 / 48},
-     {-1.0 / 8, 3.0 / 2, -11.0 / 4, 3.0 / 2, -1.0 / 8}},
-    {{-3.0 / 800 + 11.0 * GKS_SQ15 / 1200, 29.0 / 600 - 41.0 * GKS_SQ15 / 600, 1093.0 / 1200,
-      29.0 / 600 + 41.0 * GKS_SQ15 / 600, -11.0 * GKS_SQ15 / 1200 - 3.0 / 800},
-     {1.0 / 15 - GKS_SQ15 / 100, -19.0 / 30 + 7.0 * GKS_SQ15 / 50, -13.0 * GKS_SQ15 / 50,
-      7.0 * GKS_SQ15 / 50 + 19.0 / 30, -1.0 / 15 - GKS_SQ15 / 100},
-     {-GKS_SQ15 / 20 - 1.0 / 20, GKS_SQ15 / 10 + 6.0 / 5, -23.0 / 10, 6.0 / 5 - GKS_SQ15 / 10,
-      -1.0 / 20 + GKS_SQ15 / 20}}};
-// three-point Gauss-Legendre weights on the face
-__device__ __constant__ double GW[3] = {5.0 / 18, 8.0 / 18, 5.0 / 18};
-
-// ---------------------------------------------------------------------------
-// Normal reconstruction of one face from its 4-cell stencil, in the face's local frame.
-// in[v][0..3] = W_{i-1..i+2}, in[v][4..7] = dx W'_{i-1..i+2}.
-// rec[0] W0, rec[1] dW0/dn, rec[2] d2W0/dn2, rec[3] Wl, rec[4] dWl/dn, rec[5] Wr, rec[6] dWr/dn
-// ---------------------------------------------------------------------------
-template <typename R, int DIM, int ORDER, bool WENO>
-__device__ __forceinline__ void normal_recon(const R in[DIM + 2][8], R h, R gamma, R eps,
-                                             R rec[WENO ? 7 : 3][DIM + 2]) {
-  const int N = DIM + 2;
-  const R ih = R(1) / h;
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    R val, dh, ddh2;
-    linear_recon<R, ORDER>(in[v][0], in[v][1], in[v][2], in[v][3], in[v][4], in[v][5], in[v][6],
-                           in[v][7], val, dh, ddh2);
-    rec[0][v] = val;
-    rec[1][v] = dh * ih;
-    rec[2][v] = ddh2 * ih * ih;
-  }
-  if (WENO) {
-    R Wm[N];
-#pragma unroll
-    for (int v = 0; v < N; ++v) Wm[v] = R(0.5) * (in[v][1] + in[v][2]);
-    Eig<R, DIM> e = eig_at<R, DIM>(Wm, gamma);
-    R q[8][N];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      R col[N];
-#pragma unroll
-      for (int v = 0; v < N; ++v) col[v] = in[v][m];
-      eig_left<R, DIM>(e, col, q[m]);
-    }
-    R lv[N], ld[N], rv[N], rd[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      weno_left<R, ORDER>(q[0][k], q[1][k], q[2][k], q[3][k], q[4][k], q[5][k], q[6][k], q[7][k],
-                          eps, lv[k], ld[k]);
-      // right state: mirror about the interface (cells swap, slopes change sign)
-      R d;
-      weno_left<R, ORDER>(q[3][k], q[2][k], q[1][k], q[0][k], -q[7][k], -q[6][k], -q[5][k],
-                          -q[4][k], eps, rv[k], d);
-      rd[k] = -d;
-    }
-    R t[N];
-    eig_right<R, DIM>(e, lv, t);
-#pragma unroll
-    for (int v = 0; v < N; ++v) rec[3][v] = t[v];
-    eig_right<R, DIM>(e, ld, t);
-#pragma unroll
-    for (int v = 0; v < N; ++v) rec[4][v] = t[v] * ih;
-    eig_right<R, DIM>(e, rv, t);
-#pragma unroll
-    for (int v = 0; v < N; ++v) rec[5][v] = t[v];
-    eig_right<R, DIM>(e, rd, t);
-#pragma unroll
-    for (int v = 0; v < N; ++v) rec[6][v] = t[v] * ih;
-  }
-}
-
-template <int DIM>
-__device__ __forceinline__ void swap_uv(double* w) {
-  if (DIM == 2) { double t = w[1]; w[1] = w[2]; w[2] = t; }
-}
 
 // Write the stage outputs of one face; o = output base, stride = faces per plane.
 template <int DIM>
@@ -158,7 +68,7 @@ __global__ void __launch_bounds__(128) faces_1d_kernel(FaceArgs a) {
     }
   }
   R rec[WENO ? 7 : 3][N];
-  normal_recon<R, 1, ORDER, WENO>(in, R(a.dn), R(a.P.gamma), R(a.P.weno_eps), rec);
+  normal_recon<R, 1, ORDER, WENO>(in, R(a.dn), R(a.P.gamma), R(a.P.weno_eps), rec, nullptr);
   PointIn<R, 1> pin;
 #pragma unroll
   for (int v = 0; v < N; ++v) {
@@ -226,7 +136,7 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
 #pragma unroll
         for (int v = 0; v < N; ++v) { in[v][o] = w[v]; in[v][4 + o] = a.dn * g[v]; }
       }
-      normal_recon<R, 2, ORDER, WENO>(in, R(a.dn), R(a.P.gamma), R(a.P.weno_eps), rec);
+      normal_recon<R, 2, ORDER, WENO>(in, R(a.dn), R(a.P.gamma), R(a.P.weno_eps), rec, nullptr);
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q)

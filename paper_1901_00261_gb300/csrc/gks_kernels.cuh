@@ -35,7 +35,41 @@ struct UpdateArgs {
   double idx, idy;
 };
 
+// FP32-bulk face sweep: reads the FP32 mirror of the state, writes FP32 deltas.
+struct FaceArgs32 {
+  const float* M;      // mirror [hi (nv planes) | lo (nv planes) | ...]
+  const float* Mn;     // mirrored gradient along the face normal [nv][ny][nx]
+  const double* fref;  // per-cell FP64 Euler fluxes [F | G][nv][ncell]
+  void* out;           // face buffer (FP64 planes, then FP32 planes)
+  const double* dtp;
+  unsigned int* status;
+  int nx, ny, bcx, bcy;
+  double dn, dtan;
+  float dnf, itanf, gammaf, epsf;   // single-precision copies (dn, 1/dtan, gamma, WENO eps)
+  int stage;
+  PhysParams P;
+};
+
+// FP32-bulk cell update: FP64 accumulation; writes the next mirror.
+struct UpdateArgs32 {
+  const double* W;     // FP64 state W^n (stage 1)
+  const float* fx;
+  const float* fy;
+  double* Ws;
+  double* acc;
+  float* M;            // mirror written for the next sweep
+  double* fref;        // per-cell FP64 Euler fluxes [F | G][nv][ncell] of the step's state
+  const double* dtp;
+  int nx, ny, bcx, bcy;
+  double idx, idy, gamma;
+};
+
 // launchers (defined in the .cu units)
+cudaError_t launch_mirror_ref(const double* S, float* M, double* fref, int nx, int ny, int dim,
+                              double gamma, cudaStream_t s);
+cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool visc, cudaStream_t s);
+cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon, bool visc, cudaStream_t s);
+cudaError_t launch_update32(const UpdateArgs32& a, int dim, int stage, cudaStream_t s);
 cudaError_t launch_faces_1d(const FaceArgs& a, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_faces_2d(const FaceArgs& a, int dir, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs& a, int dim, int stage, cudaStream_t s);

@@ -1,0 +1,119 @@
+// gks_sweep.cuh -- helpers shared by the FP64 and FP32-bulk face sweeps: boundary index
+// mapping, the tangential quartic weights and the normal reconstruction of one face.
+#pragma once
+#include "gks_device.cuh"
+
+namespace gks {
+
+__device__ __forceinline__ int map_index(int i, int n, int bc) {
+  if (bc == 0) { i %= n; return i < 0 ? i + n : i; }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Tangential quartic through the averages over the five unit segments centred at -2..2:
+// weights of the value, d/ds and d2/ds2 at the Gauss points s = -sqrt(3/5)/2, 0, +sqrt(3/5)/2.
+#define GKS_SQ15 3.87298334620741688518
+__device__ __constant__ double TW[3][3][5] = {
+    {{-11.0 * GKS_SQ15 / 1200 - 3.0 / 800, 29.0 / 600 + 41.0 * GKS_SQ15 / 600, 1093.0 / 1200,
+      29.0 / 600 - 41.0 * GKS_SQ15 / 600, -3.0 / 800 + 11.0 * GKS_SQ15 / 1200},
+     {GKS_SQ15 / 100 + 1.0 / 15, -19.0 / 30 - 7.0 * GKS_SQ15 / 50, 13.0 * GKS_SQ15 / 50,
+      19.0 / 30 - 7.0 * GKS_SQ15 / 50, -1.0 / 15 + GKS_SQ15 / 100},
+     {-1.0 / 20 + GKS_SQ15 / 20, 6.0 / 5 - GKS_SQ15 / 10, -23.0 / 10, GKS_SQ15 / 10 + 6.0 / 5,
+      -GKS_SQ15 / 20 - 1.0 / 20}},
+    {{3.0 / 640, -29.0 / 480, 1067.0 / 960, -29.0 / 480, 3.0 / 640},
+     {5.0 / 48, -17.0 / 24, 0.0, 17.0 / 24, -5.0 / 48},
+     {-1.0 / 8, 3.0 / 2, -11.0 / 4, 3.0 / 2, -1.0 / 8}},
+    {{-3.0 / 800 + 11.0 * GKS_SQ15 / 1200, 29.0 / 600 - 41.0 * GKS_SQ15 / 600, 1093.0 / 1200,
+      29.0 / 600 + 41.0 * GKS_SQ15 / 600, -11.0 * GKS_SQ15 / 1200 - 3.0 / 800},
+     {1.0 / 15 - GKS_SQ15 / 100, -19.0 / 30 + 7.0 * GKS_SQ15 / 50, -13.0 * GKS_SQ15 / 50,
+      7.0 * GKS_SQ15 / 50 + 19.0 / 30, -1.0 / 15 - GKS_SQ15 / 100},
+     {-GKS_SQ15 / 20 - 1.0 / 20, GKS_SQ15 / 10 + 6.0 / 5, -23.0 / 10, 6.0 / 5 - GKS_SQ15 / 10,
+      -1.0 / 20 + GKS_SQ15 / 20}}};
+// three-point Gauss-Legendre weights on the face
+__device__ __constant__ double GW[3] = {5.0 / 18, 8.0 / 18, 5.0 / 18};
+// single-precision copies for the FP32-bulk sweeps
+__device__ __constant__ float TWf[3][3][5] = {
+    {{(float)(-11.0 * GKS_SQ15 / 1200 - 3.0 / 800), (float)(29.0 / 600 + 41.0 * GKS_SQ15 / 600), (float)(1093.0 / 1200),
+      (float)(29.0 / 600 - 41.0 * GKS_SQ15 / 600), (float)(-3.0 / 800 + 11.0 * GKS_SQ15 / 1200)},
+     {(float)(GKS_SQ15 / 100 + 1.0 / 15), (float)(-19.0 / 30 - 7.0 * GKS_SQ15 / 50), (float)(13.0 * GKS_SQ15 / 50),
+      (float)(19.0 / 30 - 7.0 * GKS_SQ15 / 50), (float)(-1.0 / 15 + GKS_SQ15 / 100)},
+     {(float)(-1.0 / 20 + GKS_SQ15 / 20), (float)(6.0 / 5 - GKS_SQ15 / 10), (float)(-23.0 / 10), (float)(GKS_SQ15 / 10 + 6.0 / 5),
+      (float)(-GKS_SQ15 / 20 - 1.0 / 20)}},
+    {{(float)(3.0 / 640), (float)(-29.0 / 480), (float)(1067.0 / 960), (float)(-29.0 / 480), (float)(3.0 / 640)},
+     {(float)(5.0 / 48), (float)(-17.0 / 24), 0.0f, (float)(17.0 / 24), (float)(-5.0 / 48)},
+     {(float)(-1.0 / 8), (float)(3.0 / 2), (float)(-11.0 / 4), (float)(3.0 / 2), (float)(-1.0 / 8)}},
+    {{(float)(-3.0 / 800 + 11.0 * GKS_SQ15 / 1200), (float)(29.0 / 600 - 41.0 * GKS_SQ15 / 600), (float)(1093.0 / 1200),
+      (float)(29.0 / 600 + 41.0 * GKS_SQ15 / 600), (float)(-11.0 * GKS_SQ15 / 1200 - 3.0 / 800)},
+     {(float)(1.0 / 15 - GKS_SQ15 / 100), (float)(-19.0 / 30 + 7.0 * GKS_SQ15 / 50), (float)(-13.0 * GKS_SQ15 / 50),
+      (float)(7.0 * GKS_SQ15 / 50 + 19.0 / 30), (float)(-1.0 / 15 - GKS_SQ15 / 100)},
+     {(float)(-GKS_SQ15 / 20 - 1.0 / 20), (float)(GKS_SQ15 / 10 + 6.0 / 5), (float)(-23.0 / 10), (float)(6.0 / 5 - GKS_SQ15 / 10),
+      (float)(-1.0 / 20 + GKS_SQ15 / 20)}}};
+__device__ __constant__ float GWf[3] = {(float)(5.0 / 18), (float)(8.0 / 18), (float)(5.0 / 18)};
+
+// ---------------------------------------------------------------------------
+// Normal reconstruction of one face from its 4-cell stencil, in the face's local frame.
+// in[v][0..3] = W_{i-1..i+2}, in[v][4..7] = dx W'_{i-1..i+2}.
+// rec[0] W0, rec[1] dW0/dn, rec[2] d2W0/dn2, rec[3] Wl, rec[4] dWl/dn, rec[5] Wr, rec[6] dWr/dn
+// ---------------------------------------------------------------------------
+// base != nullptr: in[v][0..3] are differences from the state base (the eigenvectors of the
+// characteristic projection are then taken at base + the mean difference).
+template <typename R, int DIM, int ORDER, bool WENO>
+__device__ __forceinline__ void normal_recon(const R in[DIM + 2][8], R h, R gamma, R eps,
+                                             R rec[WENO ? 7 : 3][DIM + 2], const R* base) {
+  const int N = DIM + 2;
+  const R ih = R(1) / h;
+#pragma unroll
+  for (int v = 0; v < N; ++v) {
+    R val, dh, ddh2;
+    linear_recon<R, ORDER>(in[v][0], in[v][1], in[v][2], in[v][3], in[v][4], in[v][5], in[v][6],
+                           in[v][7], val, dh, ddh2);
+    rec[0][v] = val;
+    rec[1][v] = dh * ih;
+    rec[2][v] = ddh2 * ih * ih;
+  }
+  if (WENO) {
+    R Wm[N];
+#pragma unroll
+    for (int v = 0; v < N; ++v) Wm[v] = R(0.5) * (in[v][1] + in[v][2]) + (base ? base[v] : R(0));
+    Eig<R, DIM> e = eig_at<R, DIM>(Wm, gamma);
+    R q[8][N];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      R col[N];
+#pragma unroll
+      for (int v = 0; v < N; ++v) col[v] = in[v][m];
+      eig_left<R, DIM>(e, col, q[m]);
+    }
+    R lv[N], ld[N], rv[N], rd[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      weno_left<R, ORDER>(q[0][k], q[1][k], q[2][k], q[3][k], q[4][k], q[5][k], q[6][k], q[7][k],
+                          eps, lv[k], ld[k]);
+      // right state: mirror about the interface (cells swap, slopes change sign)
+      R d;
+      weno_left<R, ORDER>(q[3][k], q[2][k], q[1][k], q[0][k], -q[7][k], -q[6][k], -q[5][k],
+                          -q[4][k], eps, rv[k], d);
+      rd[k] = -d;
+    }
+    R t[N];
+    eig_right<R, DIM>(e, lv, t);
+#pragma unroll
+    for (int v = 0; v < N; ++v) rec[3][v] = t[v];
+    eig_right<R, DIM>(e, ld, t);
+#pragma unroll
+    for (int v = 0; v < N; ++v) rec[4][v] = t[v] * ih;
+    eig_right<R, DIM>(e, rv, t);
+#pragma unroll
+    for (int v = 0; v < N; ++v) rec[5][v] = t[v];
+    eig_right<R, DIM>(e, rd, t);
+#pragma unroll
+    for (int v = 0; v < N; ++v) rec[6][v] = t[v] * ih;
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ void swap_uv(double* w) {
+  if (DIM == 2) { double t = w[1]; w[1] = w[2]; w[2] = t; }
+}
+
+}  // namespace gks

@@ -16,6 +16,7 @@ from . import build as _build
 
 GKS_OK, GKS_EINVAL, GKS_ECUDA, GKS_ENOMEM, GKS_ENONPHYSICAL, GKS_ETIMEOUT = 0, -1, -2, -3, -4, -5
 RECON_LINEAR, RECON_WENOZ = 0, 1
+PREC_FP64, PREC_FP32_BULK = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 
 _lock = threading.Lock()
@@ -121,9 +122,11 @@ class Solver:
     def __init__(self, nx: int, ny: int = 1, gamma: float = 1.4, mu: float = 0.0, Pr: float = 1.0,
                  order: int = 6, recon: int = RECON_LINEAR, x0: float = 0.0, x1: float = 1.0,
                  y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
-                 weno_eps: float = 1e-12, use_graph: bool = True, stream=None):
+                 weno_eps: float = 1e-12, use_graph: bool = True, stream=None,
+                 precision: int = PREC_FP64):
         L = lib()
         o = default_opts()
+        o.precision = precision
         o.x0, o.x1, o.y0, o.y1 = x0, x1, y0, y1
         o.bc_x, o.bc_y = bc_x, bc_y
         o.weno_eps = weno_eps

@@ -1,0 +1,124 @@
+"""FP32-bulk form against the FP64 form (both through the C ABI) and against exact solutions.
+
+The FP32-bulk form runs the face-sweep arithmetic in single precision on differences from a
+reference cell and keeps the time coefficients and the MSMD accumulation in FP64.  Its
+error is therefore set by single-precision rounding of those differences (about 1e-7 of
+dx |grad W| per face), not by the scheme.  Bounds below: per step against the FP64 form
+(slopes relative to the scale max|W|/dx of their difference quotient), exact conservation,
+and accuracy against the exact solutions where FP32 rounding is not yet dominant.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1901_00261_gb300 import gks, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gks.lib()
+
+
+def rel(a, b, floor=None):
+    worst = 0.0
+    for v in range(b.shape[0]):
+        scale = max(np.abs(b[v]).max(), 1e-300)
+        if floor is not None:
+            scale = max(scale, floor[v])
+        worst = max(worst, np.abs(a[v] - b[v]).max() / scale)
+    return worst
+
+
+def fp32_vs_fp64(st, nsteps=1):
+    A = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    B = gks.Solver.from_state(st, precision=gks.PREC_FP64)
+    dt = 0.3 / B.max_wavespeed()
+    A.steps(dt, nsteps)
+    B.steps(dt, nsteps)
+    a, b = A.get_state(), B.get_state()
+    errs = [rel(a[0], b[0])]
+    for k, h in ((1, st.dx), (2, st.dy)):
+        if b[k] is not None:
+            errs.append(rel(a[k], b[k], [np.abs(b[0][v]).max() / h for v in range(b[0].shape[0])]))
+    return errs, a, st
+
+
+# (name, input, bound for W, bound for the slopes); the bounds are ~10x the differences
+# measured on a GB300 (linear paths ~2e-10 / ~1e-8, WENO-Z ~1e-7, NS ~1e-6).
+CASES = [
+    ("linear 1D 6th N=80", lambda: inputs.density_wave_1d(80, order=6), 3e-9, 3e-8),
+    ("linear 1D 8th N=1000", lambda: inputs.density_wave_1d(1000, order=8), 3e-9, 3e-8),
+    ("linear 2D 8th 64^2", lambda: inputs.isentropic_vortex_2d(64, order=8), 3e-8, 3e-7),
+    ("linear 2D 6th 37x29", lambda: inputs.isentropic_vortex_2d(37, order=6, ny=29), 3e-8, 3e-7),
+    ("WENO-Z 1D Sod N=1000", lambda: inputs.sod_1d(1000), 2e-6, 2e-6),
+    ("WENO-Z 1D Shu-Osher N=400", lambda: inputs.shu_osher_1d(400), 2e-6, 2e-6),
+    ("WENO-Z 2D vortex 64^2", lambda: inputs.isentropic_vortex_2d(64, order=8, recon=1), 3e-7, 2e-6),
+    ("NS WENO-Z shear layer 64^2", lambda: inputs.shear_layer_2d(64), 2e-5, 2e-5),
+]
+
+
+@pytest.mark.parametrize("name,make,tolw,tols", CASES, ids=[c[0] for c in CASES])
+def test_fp32_bulk_one_step_close_to_fp64(name, make, tolw, tols):
+    errs, _, _ = fp32_vs_fp64(make())
+    assert errs[0] <= tolw, f"{name}: W {errs[0]:.3e}"
+    assert max(errs[1:]) <= tols, f"{name}: slopes {errs[1:]}"
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.isentropic_vortex_2d(96, order=8),
+                                  lambda: inputs.shear_layer_2d(64),
+                                  lambda: inputs.density_wave_1d(200, order=8, recon=1)])
+def test_fp32_bulk_conserves_exactly(make):
+    st = make()
+    A = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    dt = 0.3 / A.max_wavespeed()
+    A.steps(dt, 5)
+    W, _, _ = A.get_state()
+    m0 = st.W.sum(axis=(1, 2))
+    assert np.abs(W.sum(axis=(1, 2)) - m0).max() <= 1e-13 * np.abs(st.W).sum(axis=(1, 2)).max()
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_fp32_bulk_vortex_accuracy_within_2x_of_fp64(n):
+    """Isentropic vortex, 8th order, t = 1: L1 density error of the FP32-bulk form within a
+    factor 2 of the FP64 form (on finer grids FP32 rounding, ~2e-8 at t = 1, dominates)."""
+    res = {}
+    for prec in (gks.PREC_FP64, gks.PREC_FP32_BULK):
+        st = inputs.isentropic_vortex_2d(n, order=8)
+        S = gks.Solver.from_state(st, precision=prec)
+        T = 1.0
+        ns = math.ceil(T / (0.3 / S.max_wavespeed()))
+        S.steps(T / ns, ns)
+        W, _, _ = S.get_state()
+        res[prec] = np.abs(W[0] - inputs.vortex_exact_avg(n, T)[0]).mean()
+    assert res[gks.PREC_FP32_BULK] <= 2.0 * res[gks.PREC_FP64], res
+
+
+def test_fp32_bulk_density_wave_error_floor():
+    """Table 1 configuration (6th-order linear, N = 80, t = 2): the FP64 form gives the
+    printed 1.220e-10; the FP32-bulk form stays below 3e-9 (its rounding floor)."""
+    N = 80
+    st = inputs.density_wave_1d(N, order=6)
+    S = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    n = math.ceil(2.0 / (0.3 * (2.0 / N) ** 1.5))
+    S.steps(2.0 / n, n)
+    W, _, _ = S.get_state()
+    L1 = np.abs(W[0, 0] - inputs.density_wave_exact_rho(N, 2.0)).mean()
+    assert L1 < 3e-9
+
+
+def test_fp32_bulk_set_state_refreshes_mirror():
+    st = inputs.isentropic_vortex_2d(48, order=8)
+    A = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    A.steps(0.01, 3)
+    A.set_state(st.W, st.Wx, st.Wy)     # back to the initial state
+    A.steps(0.01, 2)
+    B = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    B.steps(0.01, 2)
+    for a, b in zip(A.get_state(), B.get_state()):
+        assert np.array_equal(a, b)
