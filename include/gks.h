@@ -121,6 +121,64 @@ int gks_probe_alu_peak(int fp64, double* flops_per_s);
 /* Release everything the context owns.  NULL is ignored. */
 void gks_destroy(gks_ctx* ctx);
 
+/* ---- Batches: many independent problems of uneven size, FP32-bulk form ----
+ * Every problem is advanced by the same two-stage scheme as gks_step in the FP32-bulk form.
+ * One step of the whole batch is one persistent, cooperative kernel launch over a work-list
+ * of tiles ordered by phase (stage-1 sweeps, stage-1 updates, stage-2 sweeps, stage-2
+ * updates); a tile waits (bounded by a clock budget; GKS_ETIMEOUT if it runs out) until the
+ * previous phase of its own problem is complete.  The step is replayed from a CUDA graph.
+ * A problem advanced in a batch runs the same arithmetic as when advanced alone with
+ * precision GKS_PREC_FP32_BULK; the two agree to single-precision rounding (the compiler
+ * fuses multiply-adds differently in the two kernels), not bitwise.  Within a batch the
+ * result does not depend on the configuration or on the order tiles are handed out. */
+typedef struct gks_batch gks_batch;
+typedef struct gks_problem {
+  int nx, ny;              /* cells; ny == 1: 1D (nx >= 5; 2D: ny >= 5) */
+  int order, recon;        /* 6 | 8; GKS_RECON_LINEAR | GKS_RECON_WENOZ */
+  double gamma, mu, Pr;    /* as in gks_create */
+  double x0, x1, y0, y1;   /* domain */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC | GKS_BC_TRANSMISSIVE */
+} gks_problem;
+
+/* Create a batch of n problems (copied); device memory for all of them is one allocation.
+ * Returns NULL on error (gks_batch_last_error). */
+gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream);
+const char* gks_batch_last_error(void);
+/* Host state of problem i ([nvar][ny][nx] float64; Wy NULL in 1D).  Synchronous.
+ * set_state also clears problem i's non-physical flag; get_state returns GKS_ENONPHYSICAL
+ * (after copying) when problem i has met a non-physical state. */
+int gks_batch_set_state(gks_batch* b, int i, const double* W, const double* Wx, const double* Wy);
+int gks_batch_get_state(gks_batch* b, int i, double* W, double* Wx, double* Wy);
+/* Advance every problem nsteps steps; dt[i] > 0 is problem i's step (asynchronous). */
+int gks_batch_steps(gks_batch* b, const double* dt, int nsteps);
+int gks_batch_step(gks_batch* b, const double* dt);
+/* out[i] = max (|U|+c)/dx (+ (|V|+c)/dy) of problem i.  Synchronises. */
+int gks_batch_max_wavespeed(gks_batch* b, double* out);
+/* Waits for the batch.  GKS_ETIMEOUT if a dependency wait ran out; GKS_ENONPHYSICAL if any
+ * problem met a non-physical interface state (rho <= 0 or p <= 0): such a problem is frozen
+ * from that step on (its state is not advanced further and is not meaningful) while every
+ * other problem keeps stepping; the message names the problems. */
+int gks_batch_sync(gks_batch* b);
+/* out[i] (n ints) = GKS_OK or GKS_ENONPHYSICAL for problem i.  Synchronises; returns
+ * GKS_ETIMEOUT if a dependency wait ran out. */
+int gks_batch_problem_status(gks_batch* b, int* out);
+/* Tile shape of the persistent launch: faces (cells) per thread 1 or 2, resident blocks per SM. */
+int gks_batch_config(gks_batch* b, int* faces_per_thread, int* blocks_per_sm);
+int gks_batch_set_config(gks_batch* b, int faces_per_thread, int blocks_per_sm);
+/* Autotuner: time `steps` steps for every tile shape candidate on this batch (the states are
+ * restored afterwards), keep the fastest, cache it for batches of the same shape, and write a
+ * table of the timings to report (may be NULL). */
+int gks_batch_autotune(gks_batch* b, const double* dt, int steps, char* report, int report_len);
+/* Clear every status flag (the frozen problems step again) and restore the default wait
+ * budget and problem table. */
+int gks_batch_reset(gks_batch* b);
+/* Test hook for the timeout path: problem `problem`'s items of phase `phase` + 1 will wait for
+ * one more producer of phase `phase` than exists, with a wait budget of wait_seconds (<= 10);
+ * the next step then ends with every such wait running out and gks_batch_sync returning
+ * GKS_ETIMEOUT, with the context still usable (gks_batch_reset restores it). */
+int gks_batch_debug_missing_producer(gks_batch* b, int problem, int phase, double wait_seconds);
+void gks_batch_destroy(gks_batch* b);
+
 /* ---- One step without any allocation (the paper has no counterpart) ----
  * For callers that cannot call cudaMalloc: code inside a memory pool it does not own, a
  * plug-in whose host forbids device allocation after start-up, or a real-time loop where

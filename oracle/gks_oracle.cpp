@@ -664,7 +664,9 @@ int map_index(int i, int n, int bc) {
 // Outputs are line averages over the face: W0, dW0/dn, d2W0/dn2, Wl, dWl/dn, Wr, dWr/dn.
 struct FaceRecon { double W0[4], W0n[4], W0nn[4], Wl[4], Wln[4], Wr[4], Wrn[4]; };
 
-void normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& fr) {
+// Returns false when the state the characteristic projection is taken at is not physical
+// (rho <= 0 or p <= 0): the eigenvectors do not exist there.
+bool normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& fr) {
   const Tables& T = tables();
   int oi = S.order == 6 ? 0 : 1, n = S.nv;
   for (int v = 0; v < n; ++v) {
@@ -674,17 +676,22 @@ void normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& 
   }
   if (S.recon == 0) {
     for (int v = 0; v < n; ++v) { fr.Wl[v] = fr.Wr[v] = fr.W0[v]; fr.Wln[v] = fr.Wrn[v] = fr.W0n[v]; }
-    return;
+    return true;
   }
   // characteristic projection at the mean of the two cells next to the face
   double Wm[4], R[16], L[16];
   for (int v = 0; v < n; ++v) Wm[v] = 0.5 * (in8[v][1] + in8[v][2]);
+  {
+    double ke = 0.0;
+    for (int d = 1; d <= S.dim; ++d) ke += Wm[d] * Wm[d];
+    if (!(Wm[0] > 0.0) || !(Wm[n - 1] - 0.5 * ke / Wm[0] > 0.0)) return false;
+  }
   euler_right_eigvecs(S.dim, S.ph.gamma, Wm, R);
   {
     double A[16];
     std::memcpy(A, R, sizeof(double) * n * n);
     for (int r = 0; r < n; ++r) for (int c = 0; c < n; ++c) L[r * n + c] = (r == c) ? 1.0 : 0.0;
-    if (!gauss_solve(n, A, L, n)) std::abort();
+    if (!gauss_solve(n, A, L, n)) return false;
   }
   double q[4][8];
   for (int k = 0; k < n; ++k)
@@ -706,6 +713,7 @@ void normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& 
     }
     fr.Wl[v] = a; fr.Wln[v] = b / h; fr.Wr[v] = c; fr.Wrn[v] = d / h;
   }
+  return true;
 }
 
 // Per-face results of one stage, Gauss-averaged over the face.
@@ -734,7 +742,10 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
         in8[v][o] = W[cidx(S, v, j, ci)];
         in8[v][4 + o] = S.dx * Wx[cidx(S, v, j, ci)];
       }
-    normal_recon(S, in8, S.dx, rx[idx]);
+    if (!normal_recon(S, in8, S.dx, rx[idx])) {
+#pragma omp critical
+      ok = false;
+    }
   }
   fx.assign((size_t)(nx + 1) * ny, FaceOut());
 #pragma omp parallel for schedule(static)
@@ -799,7 +810,10 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       swapuv(dim, w); swapuv(dim, wy);
       for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dy * wy[v]; }
     }
-    normal_recon(S, in8, S.dy, ry[idx]);
+    if (!normal_recon(S, in8, S.dy, ry[idx])) {
+#pragma omp critical
+      ok = false;
+    }
   }
   fy.assign((size_t)(ny + 1) * nx, FaceOut());
 #pragma omp parallel for schedule(static)

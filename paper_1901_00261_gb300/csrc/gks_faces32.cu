@@ -1,347 +1,7 @@
-// gks_faces32.cu -- FP32-bulk form of the face sweeps and cell updates.
-//
-// The reconstruction, WENO-Z and gas-kinetic arithmetic of a face runs in single precision
-// on differences from a reference state: the face's left cell (cell f-1 for face f).  The
-// state is read from an FP32 mirror that stores every FP64 cell average as a float pair
-// hi + lo (hi = float(W), lo = float(W - hi)), so differences of neighbouring cells,
-// (hi_k - hi_ref) + (lo_k - lo_ref), keep single-precision accuracy relative to the
-// difference.  Slopes are mirrored as floats.
-//
-// A face writes single-precision deltas:
-//   stage 1: comp 0 dF = F - F_Euler(W_ref), comp 1 F_t,
-//            comp 2 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt,
-//            comp 3 dLambda = W0 - W_ref + dt W_t + dt^2/6 W_tt
-//   stage 2: comp 0 F_t*, comp 1 W_tt*
-// and the cell update adds the FP64 reference parts (F_Euler(W_ref), W_ref), so the MSMD
-// accumulation of cell averages and slopes, and conservation, stay in FP64.  The
-// time-integration coefficients of the exponential terms are FP64 (gks_device.cuh).
-#include "gks_kernels.cuh"
-#include "gks_sweep.cuh"
+// gks_faces32.cu -- standalone launches of the FP32-bulk sweeps and updates (gks_sweep32.cuh).
+#include "gks_sweep32.cuh"
 
 namespace gks {
-
-template <int DIM>
-__device__ __forceinline__ void swap_uv_f(float* w) {
-  if (DIM == 2) { float t = w[1]; w[1] = w[2]; w[2] = t; }
-}
-
-// Face outputs of the FP32-bulk sweeps (face buffer viewed as FP64 planes then FP32 planes):
-//   stage 1: FP64 Phi = dt/2 (F_ref + dF) + dt^2/8 F_t, FP64 Psi = dt (F_ref + dF) + dt^2/6 F_t,
-//            FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt, FP32 dLambda (dt, dt^2/6)
-//   stage 2: FP64 Theta = dt^2/3 F_t*, FP32 T = dt^2/3 W_tt*
-// F_ref is the FP64 Euler flux of the face's reference cell.  Writing the flux parts once per
-// face in FP64 makes their differences across a cell telescope to FP64 rounding, so the
-// FP64 accumulation of the cell averages conserves exactly.
-template <int DIM>
-__device__ __forceinline__ void write_face32(void* outv, long face, long nfaces, int stage, double dt,
-                                             const double* Fref, const float* F, const float* Ft,
-                                             const float* dW0, const float* Wt, const float* Wtt) {
-  const int N = DIM + 2;
-  double* o64 = static_cast<double*>(outv);
-  if (stage == 1) {
-    float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
-    const double h = 0.5 * dt, h2 = 0.125 * dt * dt, s6 = dt * dt / 6.0;
-    const float hf = (float)h, h2f = (float)h2, dtf = (float)dt, s6f = (float)s6;
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      double Fv = Fref[v] + (double)F[v];
-      double Ftv = (double)Ft[v];
-      o64[(0L * N + v) * nfaces + face] = h * Fv + h2 * Ftv;
-      o64[(1L * N + v) * nfaces + face] = dt * Fv + s6 * Ftv;
-      o32[(0L * N + v) * nfaces + face] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
-      o32[(1L * N + v) * nfaces + face] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
-    }
-  } else {
-    float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
-    const double s3 = dt * dt / 3.0;
-    const float s3f = (float)s3;
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      o64[(0L * N + v) * nfaces + face] = s3 * (double)Ft[v];
-      o32[v * nfaces + face] = s3f * Wtt[v];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// 1D FP32-bulk sweep: one thread per face f = 0..nx.
-// ---------------------------------------------------------------------------
-template <int ORDER, bool WENO, bool VISC>
-__global__ void __launch_bounds__(128) faces_1d_f32_kernel(FaceArgs32 a) {
-  const int N = 3;
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f > a.nx) return;
-  const double dt = *a.dtp;
-  const long ncell = a.nx;
-  const long L = N * ncell;
-  float in[N][8], ref[N];
-  int cref = map_index(f - 1, a.nx, a.bcx);
-  float rlo[N];
-#pragma unroll
-  for (int v = 0; v < N; ++v) { ref[v] = a.M[v * ncell + cref]; rlo[v] = a.M[L + v * ncell + cref]; }
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    int c = map_index(f - 2 + o, a.nx, a.bcx);
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      in[v][o] = (a.M[v * ncell + c] - ref[v]) + (a.M[L + v * ncell + c] - rlo[v]);
-      in[v][4 + o] = a.dnf * a.Mn[v * ncell + c];
-    }
-  }
-  float rec[WENO ? 7 : 3][N];
-  normal_recon<float, 1, ORDER, WENO>(in, a.dnf, a.gammaf, a.epsf, rec, ref);
-  PointIn<float, 1> pin;
-  float d0[N];
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    d0[v] = rec[0][v];
-    pin.W0[v] = ref[v] + rec[0][v]; pin.W0x[v] = rec[1][v]; pin.W0xx[v] = rec[2][v];
-    pin.Wl[v] = ref[v] + (WENO ? rec[3][v] : rec[0][v]);
-    pin.Wlx[v] = WENO ? rec[4][v] : rec[1][v];
-    pin.Wr[v] = ref[v] + (WENO ? rec[5][v] : rec[0][v]);
-    pin.Wrx[v] = WENO ? rec[6][v] : rec[1][v];
-  }
-  PointOut<float, 1> po;
-  bool ok = gks_point<float, 1, WENO, VISC, true>(a.P, pin, dt, po, ref, d0);
-  if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
-  double Fref[N] = {0.0, 0.0, 0.0};
-  if (a.stage == 1) {
-#pragma unroll
-    for (int v = 0; v < N; ++v) Fref[v] = a.fref[v * ncell + cref];
-  }
-  write_face32<1>(a.out, f, a.nx + 1, a.stage, dt, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
-}
-
-// ---------------------------------------------------------------------------
-// 2D FP32-bulk sweep (same tiling as the FP64 sweep).  Each reconstruction slot keeps its
-// reference (hi, lo) in shared memory; the face's Gauss points use the reference of the
-// face's own row (tangential slot 2), and the other slots' references enter as
-// (hi_t - hi_c) + (lo_t - lo_c).
-// ---------------------------------------------------------------------------
-constexpr int TA32 = 32, TB32 = 4;
-
-template <int DIR>
-struct Tile32 {
-  static constexpr int SA = DIR == 0 ? TA32 : TA32 + 4;
-  static constexpr int SB = DIR == 0 ? TB32 + 4 : TB32;
-  static constexpr int NS = SA * SB;
-};
-
-template <int ORDER, bool WENO, bool VISC, int DIR>
-__global__ void __launch_bounds__(TA32 * TB32) faces_2d_f32_kernel(FaceArgs32 a) {
-  const int N = 4;
-  const int NQ = WENO ? 7 : 3;
-  typedef Tile32<DIR> T;
-  extern __shared__ float smf[];   // [NQ + 2][N][NS]: reconstruction, then ref hi, ref lo
-  float* sref = smf + NQ * N * T::NS;
-  float* sreflo = sref + N * T::NS;
-  const double dt = *a.dtp;
-  const long ncell = (long)a.nx * a.ny;
-  const long L = N * ncell;
-  const int tid = threadIdx.y * TA32 + threadIdx.x;
-  const int nthreads = TA32 * TB32;
-  const int nn = DIR == 0 ? a.nx + 1 : a.ny + 1;
-
-  for (int s = tid; s < T::NS; s += nthreads) {
-    int sa = s % T::SA, sb = s / T::SA;
-    int fn, ct;
-    if (DIR == 0) { fn = blockIdx.x * TA32 + sa; ct = map_index(blockIdx.y * TB32 + sb - 2, a.ny, a.bcy); }
-    else { ct = map_index(blockIdx.x * TA32 + sa - 2, a.nx, a.bcx); fn = blockIdx.y * TB32 + sb; }
-    float rec[NQ][N];
-    float ref[N], rlo[N];
-    if (fn < nn) {
-      long cr;
-      if (DIR == 0) cr = (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx);
-      else cr = (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
-#pragma unroll
-      for (int v = 0; v < N; ++v) { ref[v] = a.M[v * ncell + cr]; rlo[v] = a.M[L + v * ncell + cr]; }
-      if (DIR == 1) { swap_uv_f<2>(ref); swap_uv_f<2>(rlo); }
-      float in[N][8];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        long c;
-        if (DIR == 0) c = (long)ct * a.nx + map_index(fn - 2 + o, a.nx, a.bcx);
-        else c = (long)map_index(fn - 2 + o, a.ny, a.bcy) * a.nx + ct;
-        float hi[N], lo[N], g[N];
-#pragma unroll
-        for (int v = 0; v < N; ++v) {
-          hi[v] = a.M[v * ncell + c]; lo[v] = a.M[L + v * ncell + c]; g[v] = a.Mn[v * ncell + c];
-        }
-        if (DIR == 1) { swap_uv_f<2>(hi); swap_uv_f<2>(lo); swap_uv_f<2>(g); }
-#pragma unroll
-        for (int v = 0; v < N; ++v) {
-          in[v][o] = (hi[v] - ref[v]) + (lo[v] - rlo[v]);
-          in[v][4 + o] = a.dnf * g[v];
-        }
-      }
-      normal_recon<float, 2, ORDER, WENO>(in, a.dnf, a.gammaf, a.epsf, rec, ref);
-    } else {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int v = 0; v < N; ++v) rec[q][v] = 0.f;
-#pragma unroll
-      for (int v = 0; v < N; ++v) { ref[v] = 0.f; rlo[v] = 0.f; }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-      for (int v = 0; v < N; ++v) smf[(q * N + v) * T::NS + s] = rec[q][v];
-#pragma unroll
-    for (int v = 0; v < N; ++v) { sref[v * T::NS + s] = ref[v]; sreflo[v * T::NS + s] = rlo[v]; }
-  }
-  __syncthreads();
-
-  int fn, ct;
-  if (DIR == 0) { fn = blockIdx.x * TA32 + threadIdx.x; ct = blockIdx.y * TB32 + threadIdx.y; }
-  else { ct = blockIdx.x * TA32 + threadIdx.x; fn = blockIdx.y * TB32 + threadIdx.y; }
-  const int nt = DIR == 0 ? a.ny : a.nx;
-  if (fn >= nn || ct >= nt) return;
-  int slot[5];
-#pragma unroll
-  for (int t = 0; t < 5; ++t)
-    slot[t] = DIR == 0 ? (threadIdx.y + t) * T::SA + threadIdx.x : threadIdx.y * T::SA + threadIdx.x + t;
-  // reference of this face and the other slots' reference offsets
-  float ref[N], dref[5][N];
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    ref[v] = sref[v * T::NS + slot[2]];
-    float rl = sreflo[v * T::NS + slot[2]];
-#pragma unroll
-    for (int t = 0; t < 5; ++t)
-      dref[t][v] = (sref[v * T::NS + slot[t]] - ref[v]) + (sreflo[v * T::NS + slot[t]] - rl);
-  }
-  const float it = a.itanf;
-  float F[N] = {0}, Ft[N] = {0}, dW0[N] = {0}, Wt[N] = {0}, Wtt[N] = {0};
-  bool ok = true;
-#pragma unroll 1
-  for (int g = 0; g < 3; ++g) {
-    PointIn<float, 2> pin;
-    float d0[N];
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      float s0 = 0, s1 = 0, s2 = 0, n0 = 0, n1 = 0, nn0 = 0;
-      float l0 = 0, l1 = 0, ln0 = 0, r0 = 0, r1 = 0, rn0 = 0;
-#pragma unroll
-      for (int t = 0; t < 5; ++t) {
-        const float w0 = TWf[g][0][t], w1 = TWf[g][1][t], w2 = TWf[g][2][t];
-        float q0 = smf[(0 * N + v) * T::NS + slot[t]] + dref[t][v];
-        float q1 = smf[(1 * N + v) * T::NS + slot[t]];
-        float q2 = smf[(2 * N + v) * T::NS + slot[t]];
-        s0 += w0 * q0; s1 += w1 * q0; s2 += w2 * q0;
-        n0 += w0 * q1; n1 += w1 * q1;
-        nn0 += w0 * q2;
-        if (WENO) {
-          float ql = smf[(3 * N + v) * T::NS + slot[t]] + dref[t][v];
-          float qld = smf[(4 * N + v) * T::NS + slot[t]];
-          float qr = smf[(5 * N + v) * T::NS + slot[t]] + dref[t][v];
-          float qrd = smf[(6 * N + v) * T::NS + slot[t]];
-          l0 += w0 * ql; l1 += w1 * ql; ln0 += w0 * qld;
-          r0 += w0 * qr; r1 += w1 * qr; rn0 += w0 * qrd;
-        }
-      }
-      d0[v] = s0;
-      pin.W0[v] = ref[v] + s0; pin.W0y[v] = s1 * it; pin.W0yy[v] = s2 * it * it;
-      pin.W0x[v] = n0; pin.W0xy[v] = n1 * it; pin.W0xx[v] = nn0;
-      if (WENO) {
-        pin.Wl[v] = ref[v] + l0; pin.Wly[v] = l1 * it; pin.Wlx[v] = ln0;
-        pin.Wr[v] = ref[v] + r0; pin.Wry[v] = r1 * it; pin.Wrx[v] = rn0;
-      } else {
-        pin.Wl[v] = pin.W0[v]; pin.Wly[v] = pin.W0y[v]; pin.Wlx[v] = n0;
-        pin.Wr[v] = pin.W0[v]; pin.Wry[v] = pin.W0y[v]; pin.Wrx[v] = n0;
-      }
-    }
-    PointOut<float, 2> po;
-    ok &= gks_point<float, 2, WENO, VISC, true>(a.P, pin, dt, po, ref, d0);
-    const float wg = GWf[g];
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      F[v] += wg * po.F[v]; Ft[v] += wg * po.Ft[v];
-      dW0[v] += wg * po.W0[v]; Wt[v] += wg * po.Wt[v]; Wtt[v] += wg * po.Wtt[v];
-    }
-  }
-  if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
-  if (DIR == 1) { swap_uv_f<2>(F); swap_uv_f<2>(Ft); swap_uv_f<2>(dW0); swap_uv_f<2>(Wt); swap_uv_f<2>(Wtt); }
-  long face, nfaces;
-  if (DIR == 0) { face = (long)ct * (a.nx + 1) + fn; nfaces = (long)a.ny * (a.nx + 1); }
-  else { face = (long)fn * a.nx + ct; nfaces = (long)(a.ny + 1) * a.nx; }
-  double Fref[N] = {0.0, 0.0, 0.0, 0.0};
-  if (a.stage == 1) {
-    // reference cell of the face (global frame): F for x faces, G for y faces
-    long cr = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
-                       : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
-    const double* fr = a.fref + (DIR == 0 ? 0 : L);
-#pragma unroll
-    for (int v = 0; v < N; ++v) Fref[v] = fr[v * ncell + cr];
-  }
-  write_face32<2>(a.out, face, nfaces, a.stage, dt, Fref, F, Ft, dW0, Wt, Wtt);
-}
-
-// ---------------------------------------------------------------------------
-// FP32-bulk cell updates.  Face f's reference is cell f-1 (mapped), the left (x) or lower
-// (y) neighbour; the update adds back the reference flux F_Euler(W_ref), kept per cell in
-// FP64 (written when the state is produced), and W_ref for the interface values.
-// Stage 1 accumulates the W^{n+1} and slope parts in FP64 and writes W* only as the FP32
-// mirror read by the stage-2 sweep; stage 2 writes the FP64 state, its mirror and its
-// reference fluxes.
-// ---------------------------------------------------------------------------
-template <int DIM>
-__device__ __forceinline__ void euler_fluxes64(const double* W, double gamma, double* F, double* G) {
-  const int N = DIM + 2;
-  double irho = 1.0 / W[0];
-  double U = W[1] * irho, V = DIM == 2 ? W[2] * irho : 0.0;
-  double p = (gamma - 1.0) * (W[N - 1] - 0.5 * (W[1] * U + (DIM == 2 ? W[2] * V : 0.0)));
-#pragma unroll
-  for (int k = 0; k < N; ++k) F[k] = W[k] * U;
-  F[1] += p;
-  F[N - 1] += p * U;
-  if (DIM == 2) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) G[k] = W[k] * V;
-    G[2] += p;
-    G[N - 1] += p * V;
-  }
-}
-
-// FP32 mirror and reference fluxes of one cell's FP64 state.
-template <int DIM>
-__device__ __forceinline__ void write_mirror(float* M, double* fref, long c, long ncell, const double* w,
-                                             const double* wx, const double* wy, double gamma) {
-  const int N = DIM + 2;
-  const long L = N * ncell;
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    float hi = (float)w[v];
-    M[v * ncell + c] = hi;
-    M[L + v * ncell + c] = (float)(w[v] - (double)hi);
-    M[2 * L + v * ncell + c] = (float)wx[v];
-    if (DIM == 2) M[3 * L + v * ncell + c] = (float)wy[v];
-  }
-  double F[N], G[N];
-  euler_fluxes64<DIM>(w, gamma, F, G);
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    fref[v * ncell + c] = F[v];
-    if (DIM == 2) fref[L + v * ncell + c] = G[v];
-  }
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256) mirror_ref_kernel(const double* S, float* M, double* fref,
-                                                         long ncell, double gamma) {
-  const int N = DIM + 2;
-  long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const long L = N * ncell;
-  double w[N], wx[N], wy[N];
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    w[v] = S[v * ncell + c];
-    wx[v] = S[L + v * ncell + c];
-    wy[v] = DIM == 2 ? S[2 * L + v * ncell + c] : 0.0;
-  }
-  write_mirror<DIM>(M, fref, c, ncell, w, wx, wy, gamma);
-}
 
 cudaError_t launch_mirror_ref(const double* S, float* M, double* fref, int nx, int ny, int dim,
                               double gamma, cudaStream_t s) {
@@ -350,86 +10,6 @@ cudaError_t launch_mirror_ref(const double* S, float* M, double* fref, int nx, i
   if (dim == 1) mirror_ref_kernel<1><<<blocks, 256, 0, s>>>(S, M, fref, ncell, gamma);
   else mirror_ref_kernel<2><<<blocks, 256, 0, s>>>(S, M, fref, ncell, gamma);
   return cudaGetLastError();
-}
-
-template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256) update_f32_kernel(UpdateArgs32 a) {
-  const int N = DIM + 2;
-  const long ncell = (long)a.nx * a.ny;
-  long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int j = (int)(c / a.nx), i = (int)(c - (long)j * a.nx);
-  const long nfx = (long)a.ny * (a.nx + 1), nfy = (long)(a.ny + 1) * a.nx;
-  const long fxl = (long)j * (a.nx + 1) + i, fyb = (long)j * a.nx + i, fyt = fyb + a.nx;
-  const long L = N * ncell;
-  double* accW = a.acc;
-  double* accX = a.acc + L;
-  double* accY = a.acc + 2 * L;
-  const double* x64 = reinterpret_cast<const double*>(a.fx);
-  const double* y64 = reinterpret_cast<const double*>(a.fy);
-  const double idx = a.idx, idy = a.idy;
-  if (STAGE == 1) {
-    const float* x32 = reinterpret_cast<const float*>(x64 + 2L * N * nfx);
-    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 2L * N * nfy) : nullptr;
-    const long cl = (long)j * a.nx + map_index(i - 1, a.nx, a.bcx);
-    const long cb = DIM == 2 ? (long)map_index(j - 1, a.ny, a.bcy) * a.nx + i : 0;
-    const float idxf = (float)idx, idyf = (float)idy;
-    float* M = a.M;
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      const double W = a.W[v * ncell + c];
-      const double* Phi = x64 + (0L * N + v) * nfx;
-      const double* Psi = x64 + (1L * N + v) * nfx;
-      const float dOj = x32[(0L * N + v) * nfx + fxl + 1] - x32[(0L * N + v) * nfx + fxl];
-      const float dLj = x32[(1L * N + v) * nfx + fxl + 1] - x32[(1L * N + v) * nfx + fxl];
-      const double dW = W - a.W[v * ncell + cl];
-      double ws = W - (Phi[fxl + 1] - Phi[fxl]) * idx;
-      double wa = W - (Psi[fxl + 1] - Psi[fxl]) * idx;
-      accX[v * ncell + c] = (dW + (double)dLj) * idx;
-      float wxs = ((float)dW + dOj) * idxf;
-      float wys = 0.f;
-      if (DIM == 2) {
-        const double* PhiY = y64 + (0L * N + v) * nfy;
-        const double* PsiY = y64 + (1L * N + v) * nfy;
-        const float dOy = y32[(0L * N + v) * nfy + fyt] - y32[(0L * N + v) * nfy + fyb];
-        const float dLy = y32[(1L * N + v) * nfy + fyt] - y32[(1L * N + v) * nfy + fyb];
-        const double dWy = W - a.W[v * ncell + cb];
-        ws -= (PhiY[fyt] - PhiY[fyb]) * idy;
-        wa -= (PsiY[fyt] - PsiY[fyb]) * idy;
-        accY[v * ncell + c] = (dWy + (double)dLy) * idy;
-        wys = ((float)dWy + dOy) * idyf;
-      }
-      accW[v * ncell + c] = wa;
-      // W* only as the FP32 mirror read by the stage-2 sweep
-      const float hi = (float)ws;
-      M[v * ncell + c] = hi;
-      M[L + v * ncell + c] = (float)(ws - (double)hi);
-      M[2 * L + v * ncell + c] = wxs;
-      if (DIM == 2) M[3 * L + v * ncell + c] = wys;
-    }
-  } else {
-    const float* x32 = reinterpret_cast<const float*>(x64 + 1L * N * nfx);
-    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 1L * N * nfy) : nullptr;
-    double w[N], wx[N], wy[N];
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      const double* Th = x64 + (0L * N + v) * nfx;
-      const float Ttj = x32[v * nfx + fxl + 1] - x32[v * nfx + fxl];
-      w[v] = accW[v * ncell + c] - (Th[fxl + 1] - Th[fxl]) * idx;
-      wx[v] = accX[v * ncell + c] + (double)Ttj * idx;
-      wy[v] = 0.0;
-      if (DIM == 2) {
-        const double* ThY = y64 + (0L * N + v) * nfy;
-        const float Tty = y32[v * nfy + fyt] - y32[v * nfy + fyb];
-        w[v] -= (ThY[fyt] - ThY[fyb]) * idy;
-        wy[v] = accY[v * ncell + c] + (double)Tty * idy;
-      }
-      a.Ws[v * ncell + c] = w[v];
-      a.Ws[L + v * ncell + c] = wx[v];
-      if (DIM == 2) a.Ws[2 * L + v * ncell + c] = wy[v];
-    }
-    write_mirror<DIM>(a.M, a.fref, c, ncell, w, wx, wy, a.gamma);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -454,7 +34,7 @@ cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool vi
 
 template <int ORDER, bool WENO, bool VISC, int DIR>
 static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
-  typedef Tile32<DIR> T;
+  typedef Tile32<DIR, 1> T;
   const int NQ = WENO ? 7 : 3;
   size_t shmem = sizeof(float) * (NQ + 2) * 4 * T::NS;
   static bool attr_set = false;

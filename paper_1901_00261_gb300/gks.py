@@ -70,6 +70,33 @@ SIGNATURES = {
 STATIC_MAX_NX = 16384
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("order", ctypes.c_int), ("recon", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
+
+
+_VP = ctypes.c_void_p
+SIGNATURES.update({
+    "gks_batch_create": (_VP, [ctypes.c_int, ctypes.POINTER(Problem), _VP]),
+    "gks_batch_last_error": (ctypes.c_char_p, []),
+    "gks_batch_set_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gks_batch_get_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gks_batch_steps": (ctypes.c_int, [_VP, _DP, ctypes.c_int]),
+    "gks_batch_step": (ctypes.c_int, [_VP, _DP]),
+    "gks_batch_max_wavespeed": (ctypes.c_int, [_VP, _DP]),
+    "gks_batch_sync": (ctypes.c_int, [_VP]),
+    "gks_batch_config": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "gks_batch_set_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "gks_batch_autotune": (ctypes.c_int, [_VP, _DP, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]),
+    "gks_batch_destroy": (None, [_VP]),
+    "gks_batch_reset": (ctypes.c_int, [_VP]),
+    "gks_batch_problem_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "gks_batch_debug_missing_producer": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+})
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -220,3 +247,97 @@ def probe_alu_peak(fp64: bool = True) -> float:
     v = ctypes.c_double()
     _check(lib().gks_probe_alu_peak(1 if fp64 else 0, ctypes.byref(v)))
     return v.value
+
+
+def _bcheck(rc: int):
+    if rc != GKS_OK:
+        raise GksError(rc, lib().gks_batch_last_error().decode(errors="replace"))
+
+
+class Batch:
+    """Many independent problems advanced together (FP32-bulk form, persistent launch).
+
+    ``states`` is a list of inputs.State (grid, domain, BCs, physics, order, recon)."""
+
+    def __init__(self, states, stream=None):
+        L = lib()
+        arr = (Problem * len(states))()
+        for k, st in enumerate(states):
+            arr[k] = Problem(st.nx, st.ny, st.order, st.recon, st.gamma, st.mu, st.Pr,
+                             st.x0, st.x1, st.y0, st.y1, st.bc_x, st.bc_y)
+        self._h = L.gks_batch_create(len(states), arr, stream)
+        if not self._h:
+            raise GksError(GKS_EINVAL, L.gks_batch_last_error().decode(errors="replace"))
+        self.shapes = [((2 if st.ny > 1 else 1) + 2, st.ny, st.nx) for st in states]
+        self.n = len(states)
+        for k, st in enumerate(states):
+            self.set_state(k, st.W, st.Wx, st.Wy)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().gks_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, i, W, Wx, Wy=None):
+        shp = self.shapes[i]
+        W = np.ascontiguousarray(W, dtype=np.float64).reshape(shp)
+        Wx = np.ascontiguousarray(Wx, dtype=np.float64).reshape(shp)
+        Wy = None if shp[1] == 1 else np.ascontiguousarray(Wy, dtype=np.float64).reshape(shp)
+        _bcheck(lib().gks_batch_set_state(self._h, i, _host_ptr(W), _host_ptr(Wx), _host_ptr(Wy)))
+
+    def get_state(self, i):
+        shp = self.shapes[i]
+        W, Wx = np.empty(shp), np.empty(shp)
+        Wy = np.empty(shp) if shp[1] > 1 else None
+        _bcheck(lib().gks_batch_get_state(self._h, i, _host_ptr(W), _host_ptr(Wx), _host_ptr(Wy)))
+        return W, Wx, Wy
+
+    def _dt(self, dt):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n,)))
+        return a, a.ctypes.data_as(_DP)
+
+    def steps(self, dt, n: int):
+        a, p = self._dt(dt)
+        _bcheck(lib().gks_batch_steps(self._h, p, int(n)))
+
+    def max_wavespeed(self) -> np.ndarray:
+        out = np.zeros(self.n)
+        _bcheck(lib().gks_batch_max_wavespeed(self._h, out.ctypes.data_as(_DP)))
+        return out
+
+    def sync(self):
+        _bcheck(lib().gks_batch_sync(self._h))
+
+    def config(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _bcheck(lib().gks_batch_config(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_config(self, faces_per_thread: int, blocks_per_sm: int):
+        _bcheck(lib().gks_batch_set_config(self._h, faces_per_thread, blocks_per_sm))
+
+    def problem_status(self):
+        """Per-problem status: GKS_OK, or GKS_ENONPHYSICAL for a problem that met a non-physical
+        state (frozen since)."""
+        out = np.zeros(self.n, dtype=np.int32)
+        _bcheck(lib().gks_batch_problem_status(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return out
+
+    def reset(self):
+        _bcheck(lib().gks_batch_reset(self._h))
+
+    def debug_missing_producer(self, problem: int, phase: int, wait_seconds: float):
+        _bcheck(lib().gks_batch_debug_missing_producer(self._h, problem, phase, wait_seconds))
+
+    def autotune(self, dt, steps: int = 3) -> str:
+        a, p = self._dt(dt)
+        buf = ctypes.create_string_buffer(4096)
+        _bcheck(lib().gks_batch_autotune(self._h, p, int(steps), buf, 4096))
+        return buf.value.decode()

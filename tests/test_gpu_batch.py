@@ -1,0 +1,175 @@
+"""Batched form: many problems of uneven size in one persistent launch per step.
+
+A problem advanced in a batch runs the same device code as the same problem advanced alone
+by the FP32-bulk form.  The two are compiled into different kernels, and the compiler's
+choice of fusing a multiply and an add into one FMA depends on the surrounding code, so the
+two agree to single-precision rounding of the FP32 parts (bounds below: W within 1e-7
+relative, slopes within 1e-6 of max|W|/dx), not bitwise.  Within the batch the result does
+not depend on the tile shape, the occupancy or the order in which tiles are handed out
+(bitwise).  The autotuner must not change the state; a dependency wait that cannot be
+satisfied must end in GKS_ETIMEOUT, not a hang.
+"""
+import numpy as np
+import pytest
+
+from paper_1901_00261_gb300 import gks, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gks.lib()
+
+
+def mixed_states(n=10, seed=5, n1=(100, 3000), n2=(16, 96)):
+    specs = inputs.batch_specs(n, seed=seed, n1_range=n1, n2_range=n2)
+    return [inputs.build_problem(s) for s in specs]
+
+
+TOL_W, TOL_SLOPE = 1e-7, 1e-6
+
+
+def assert_close_to_alone(got, ref, st, what):
+    W = ref[0]
+    for k, (a, b) in enumerate(zip(got, ref)):
+        if b is None:
+            continue
+        for v in range(b.shape[0]):
+            scale = np.abs(b[v]).max()
+            if k > 0:
+                h = st.dx if k == 1 else st.dy
+                scale = max(scale, np.abs(W[v]).max() / h)
+            err = np.abs(a[v] - b[v]).max() / max(scale, 1e-300)
+            assert err <= (TOL_W if k == 0 else TOL_SLOPE), f"{what}: array {k} var {v}: {err:.3e}"
+
+
+def run_alone(st, dt, nsteps):
+    S = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    S.steps(dt, nsteps)
+    return S.get_state()
+
+
+def dts_of(states):
+    out = []
+    for st in states:
+        S = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+        out.append(0.3 / S.max_wavespeed())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("fpt", [1, 2])
+def test_batch_matches_individual_runs(fpt):
+    states = mixed_states()
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    _, maxb = B.config()
+    B.set_config(fpt, maxb)
+    B.steps(dts, 3)
+    for k, st in enumerate(states):
+        assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 3), st,
+                              f"problem {k} ({st.name}, {st.nx}x{st.ny})")
+
+
+def test_batch_tile_shapes_and_occupancy_agree():
+    states = mixed_states(6, seed=9)
+    dts = dts_of(states)
+    results = []
+    for fpt, bps in ((1, 1), (2, 2), (1, 3)):
+        B = gks.Batch(states)
+        B.set_config(fpt, min(bps, B.config()[1]))
+        B.steps(dts, 2)
+        results.append([B.get_state(k) for k in range(len(states))])
+    for other in results[1:]:
+        for ga, gb in zip(results[0], other):
+            for a, b in zip(ga, gb):
+                if b is not None:
+                    assert np.array_equal(a, b)
+
+
+def test_batch_class_with_2d_weno_and_navier_stokes():
+    states = [inputs.isentropic_vortex_2d(40, order=8, recon=1, ny=33),
+              inputs.shear_layer_2d(32),
+              inputs.sod_1d(257, order=6, recon=1),
+              inputs.isentropic_vortex_2d(29, order=6, recon=0)]
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    B.steps(dts, 2)
+    for k, st in enumerate(states):
+        assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 2), st, f"problem {k}")
+
+
+def test_autotune_restores_state_and_keeps_results():
+    states = mixed_states(8, seed=11)
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    report = B.autotune(dts, steps=2)
+    assert "chosen" in report
+    fpt, bps = B.config()
+    assert fpt in (1, 2) and bps >= 1
+    B.steps(dts, 2)
+    for k, st in enumerate(states):
+        assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 2), st, f"problem {k}")
+
+
+def test_batch_max_wavespeed_matches_single():
+    states = mixed_states(5, seed=2)
+    B = gks.Batch(states)
+    ws = B.max_wavespeed()
+    for k, st in enumerate(states):
+        S = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+        assert ws[k] == S.max_wavespeed()
+
+
+def test_batch_missing_producer_times_out_and_recovers():
+    """A wait on a producer that never comes runs out of its (short) budget: the step ends,
+    gks_batch_sync reports GKS_ETIMEOUT, and after a reset the batch steps normally."""
+    states = mixed_states(4, seed=3, n1=(100, 300), n2=(16, 24))
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    B.debug_missing_producer(1, 0, 0.2)
+    B.steps(dts, 1)
+    with pytest.raises(gks.GksError) as ei:
+        B.sync()
+    assert ei.value.code == gks.GKS_ETIMEOUT
+    B.reset()
+    for k, st in enumerate(states):
+        B.set_state(k, st.W, st.Wx, st.Wy)
+    B.steps(dts, 1)
+    B.sync()
+    for k, st in enumerate(states):
+        assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 1), st, f"problem {k}")
+
+
+def test_batch_freezes_a_nonphysical_problem_and_keeps_the_rest():
+    """Toro's test 3 data (p 1000 | 0.01; the oracle meets a negative energy after one step at
+    8th order, WENO-Z, N = 200) among healthy problems: the failing problem is reported by
+    index and frozen, every other problem advances exactly as if it were alone, and
+    set_state puts the failed problem back in service."""
+    bad = inputs.riemann_1d(200, (1.0, 0.0, 1000.0), (1.0, 0.0, 0.01), 0.0, 1.0, 0.5, 1.4, 8, 1)
+    good = mixed_states(4, seed=7, n1=(100, 400), n2=(16, 32))
+    states = good[:2] + [bad] + good[2:]
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    B.steps(dts, 3)
+    with pytest.raises(gks.GksError) as ei:
+        B.sync()
+    assert ei.value.code == gks.GKS_ENONPHYSICAL and "2" in str(ei.value)
+    status = B.problem_status()
+    assert list(status) == [0, 0, gks.GKS_ENONPHYSICAL, 0, 0]
+    for k, st in enumerate(states):
+        if k != 2:
+            assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 3), st, f"problem {k}")
+    with pytest.raises(gks.GksError):
+        B.get_state(2)
+    calm = inputs.riemann_1d(200, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.0, 1.0, 0.5, 1.4, 8, 1)
+    B.set_state(2, calm.W, calm.Wx)
+    assert list(B.problem_status()) == [0] * 5
+    dt2 = dts.copy()
+    dt2[2] = dts_of([calm])[0]
+    B.steps(dt2, 1)
+    B.sync()
+    assert_close_to_alone(B.get_state(2), run_alone(calm, dt2[2], 1), calm, "restarted problem")

@@ -175,3 +175,20 @@ def test_isentropic_vortex_converges():
         errs.append(np.abs(W[0] - inputs.vortex_exact_avg(n, T)[0]).mean())
         assert abs(W[0].sum() - st.W[0].sum()) < 1e-12 * st.W[0].sum()
     assert math.log2(errs[0] / errs[1]) > 4.0, errs
+
+
+def test_nonphysical_state_is_reported_not_fatal():
+    """Toro's test 3 (p 1000 | 0.01) at 8th order, WENO-Z, N = 200: the compact linear
+    derivative that drives the equilibrium state spreads the 1e5 pressure jump two faces
+    into the cold gas, a cell average there gets a negative energy after the first step, and
+    the next step must end with the non-physical status (not an abort)."""
+    st = inputs.riemann_1d(200, (1.0, 0.0, 1000.0), (1.0, 0.0, 0.01), 0.0, 1.0, 0.5, 1.4, 8, 1)
+    S = oracle.Solver(200, 1, gamma=1.4, order=8, recon=1, bc_x=1)
+    S.set_state(st.W, st.Wx)
+    dt = 0.3 / S.max_wavespeed()
+    S.step(dt)
+    W = S.get_state()[0]
+    p = 0.4 * (W[2, 0] - 0.5 * W[1, 0] ** 2 / W[0, 0])
+    assert p.min() < 0.0
+    with pytest.raises(RuntimeError, match=r"\(-4\)"):
+        S.step(dt)
