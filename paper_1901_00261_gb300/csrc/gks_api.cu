@@ -70,6 +70,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     const long L = state_len(c);
     gks::FaceArgs32 fa;
     fa.dtp = c->d_dt; fa.status = c->d_status;
+    fa.tc = reinterpret_cast<const gks::StepTimes*>(c->d_dt);
     fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
     fa.P = c->P;
     fa.M = c->mirror;
@@ -207,6 +208,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   c->P.K = c->dim == 1 ? (3.0 - gamma) / (gamma - 1.0) : (4.0 - 2.0 * gamma) / (gamma - 1.0);
   c->P.mu = mu; c->P.Pr = Pr;
   c->P.eps_tau = o.eps_tau; c->P.C_tau = o.C_tau; c->P.weno_eps = o.weno_eps;
+  gks::set_phys_floats(c->P);
 
   cudaError_t e;
   if (o.stream) c->stream = (cudaStream_t)o.stream;
@@ -221,7 +223,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   size_t fyn = c->dim == 2 ? (size_t)4 * c->nv * (ny + 1) * nx : 0;
   struct { double** p; size_t n; } bufs[] = {
       {&c->state, (size_t)nsets * L}, {&c->stage, (size_t)nsets * L}, {&c->acc, (size_t)nsets * L},
-      {&c->fx, fxn}, {&c->fy, fyn}, {&c->d_dt, 1}};
+      {&c->fx, fxn}, {&c->fy, fyn}, {&c->d_dt, (size_t)gks::STEP_TIMES_DOUBLES}};
   for (auto& b : bufs) {
     if (b.n == 0) continue;
     e = cudaMalloc((void**)b.p, b.n * sizeof(double));
@@ -296,7 +298,7 @@ int gks_steps(gks_ctx* c, double dt, int nsteps) {
   if (nsteps == 0) return GKS_OK;
   cudaError_t e;
   if (dt != c->last_dt) {
-    e = gks::launch_set_scalar(c->d_dt, dt, c->stream);
+    e = gks::launch_set_times(reinterpret_cast<gks::StepTimes*>(c->d_dt), dt, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "dt update");
     c->last_dt = dt;
   }
@@ -336,7 +338,7 @@ int gks_steps_timed(gks_ctx* c, double dt, int nsteps, double* kernel_ms) {
   for (int k = 0; k < nl; ++k) kernel_ms[k] = 0.0;
   cudaError_t e;
   if (dt != c->last_dt) {
-    e = gks::launch_set_scalar(c->d_dt, dt, c->stream);
+    e = gks::launch_set_times(reinterpret_cast<gks::StepTimes*>(c->d_dt), dt, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "dt update");
     c->last_dt = dt;
   }

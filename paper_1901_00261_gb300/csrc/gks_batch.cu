@@ -230,6 +230,7 @@ struct gks_batch {
   double* ddt = nullptr;
   unsigned long long* dws = nullptr;
   std::vector<double> last_dt;
+  std::vector<gks::StepTimes> times;   // host copy of the per-problem step constants
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int fpt = 1, blocks_per_sm = 0, max_blocks_per_sm[2] = {0, 0}, sms = 0;
@@ -403,7 +404,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&B->dprob, sizeof(gks::BatchProblem) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&B->dcount, sizeof(unsigned) * (1 + 4 * n));
   if (e == cudaSuccess) e = cudaMalloc((void**)&B->dstatus, sizeof(unsigned) * (n + 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&B->ddt, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B->ddt, sizeof(double) * gks::STEP_TIMES_DOUBLES * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&B->dws, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(B->arena, 0, bytes, B->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->dstatus, 0, sizeof(unsigned) * (n + 1), B->stream);
@@ -428,13 +429,15 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     ph.gamma = q.gamma;
     ph.K = dim == 1 ? (3.0 - q.gamma) / (q.gamma - 1.0) : (4.0 - 2.0 * q.gamma) / (q.gamma - 1.0);
     ph.mu = q.mu; ph.Pr = q.Pr; ph.eps_tau = 0.01; ph.C_tau = 1.0; ph.weno_eps = 1e-12;
+    gks::set_phys_floats(ph);
     for (int st = 0; st < 2; ++st) {
       for (int d = 0; d < 2; ++d) {
         gks::FaceArgs32& a = d == 0 ? P.ax[st] : P.ay[st];
         a.M = mir; a.fref = fref;
         a.Mn = mir + (2 + d) * L;
         a.out = d == 0 ? (void*)fx : (void*)fy;
-        a.dtp = B->ddt + p;   // device address of this problem's dt
+        a.dtp = B->ddt + (size_t)gks::STEP_TIMES_DOUBLES * p;   // this problem's step constants
+        a.tc = reinterpret_cast<const gks::StepTimes*>(a.dtp);
         a.status = B->dstatus + 1 + p;
         a.nx = q.nx; a.ny = q.ny; a.bcx = q.bc_x; a.bcy = q.bc_y;
         a.dn = d == 0 ? dx : dy; a.dtan = d == 0 ? dy : dx;
@@ -446,7 +449,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     }
     gks::UpdateArgs32& u = P.up;
     u.W = state; u.fx = reinterpret_cast<const float*>(fx); u.fy = reinterpret_cast<const float*>(fy);
-    u.Ws = state; u.acc = acc; u.M = mir; u.fref = fref; u.dtp = B->ddt + p;
+    u.Ws = state; u.acc = acc; u.M = mir; u.fref = fref; u.dtp = B->ddt + (size_t)gks::STEP_TIMES_DOUBLES * p;
     u.nx = q.nx; u.ny = q.ny; u.bcx = q.bc_x; u.bcy = q.bc_y;
     u.idx = 1.0 / dx; u.idy = 1.0 / dy; u.gamma = q.gamma;
     P.tbx_x = (q.nx + 1 + gks::TA32 - 1) / gks::TA32;
@@ -533,8 +536,11 @@ int gks_batch_steps(gks_batch* B, const double* dt, int nsteps) {
   }
   cudaError_t e;
   if (changed) {
-    // pageable source: the copy is staged before the call returns, so the host array may change
-    e = cudaMemcpyAsync(B->ddt, dt, sizeof(double) * B->n, cudaMemcpyHostToDevice, B->stream);
+    // the step constants of every problem, from the host copy kept in the batch
+    B->times.resize(B->n);
+    for (int p = 0; p < B->n; ++p) B->times[p] = gks::step_times(dt[p]);
+    e = cudaMemcpyAsync(B->ddt, B->times.data(), sizeof(gks::StepTimes) * B->n, cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);   // times may be rewritten by the next call
     if (e != cudaSuccess) return bcuda(e, "batch dt");
     B->last_dt.assign(dt, dt + B->n);
   }

@@ -325,7 +325,8 @@ struct TimeCoef { double a0, a1, b0, b1; };
 __device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
   TimeCoef T;
   double h = 0.5 * dt, x = h / tau;
-  double S = -expm1(-x);
+  // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
+  double S = x > 40.0 ? 1.0 : -expm1(-x);
   double idt = 1.0 / dt;
   T.a0 = tau * S * (2.0 + S) * idt;
   T.b0 = -4.0 * tau * S * S * idt * idt;
@@ -361,7 +362,18 @@ __device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
 // ---------------------------------------------------------------------------
 struct PhysParams {
   double gamma, K, mu, Pr, eps_tau, C_tau, weno_eps;
+  float gammaf, Kf;   // single-precision copies of gamma and K (set with set_phys_floats)
 };
+
+inline void set_phys_floats(PhysParams& P) { P.gammaf = (float)P.gamma; P.Kf = (float)P.K; }
+
+// gamma and K in the arithmetic type R
+template <typename R> __device__ __forceinline__ R phys_gamma(const PhysParams& P);
+template <> __device__ __forceinline__ double phys_gamma<double>(const PhysParams& P) { return P.gamma; }
+template <> __device__ __forceinline__ float phys_gamma<float>(const PhysParams& P) { return P.gammaf; }
+template <typename R> __device__ __forceinline__ R phys_K(const PhysParams& P);
+template <> __device__ __forceinline__ double phys_K<double>(const PhysParams& P) { return P.K; }
+template <> __device__ __forceinline__ float phys_K<float>(const PhysParams& P) { return P.Kf; }
 
 template <typename R, int DIM>
 struct PointIn {
@@ -504,7 +516,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
                                           PointOut<R, DIM>& out, const R* ref = nullptr,
                                           const R* d0 = nullptr) {
   const int N = DIM + 2;
-  const R gamma = R(P.gamma), K = R(P.K);
+  const R gamma = phys_gamma<R>(P), K = phys_K<R>(P);
   bool ok = true;
   R W0c[N];
   R pl = R(0), pr = R(0);

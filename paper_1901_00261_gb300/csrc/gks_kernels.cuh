@@ -10,6 +10,25 @@ namespace gks {
 // Status bits written by kernels (read back by the host at synchronising calls).
 enum : unsigned int { ST_NONPHYSICAL = 1u, ST_NONFINITE = 2u };
 
+// Time constants of a step, derived from dt once per change of dt (dt first, so a kernel
+// that needs only dt reads the first double).  The MSMD weights of Sec. 2.3: dt/2 and
+// dt^2/8 (W*), dt and dt^2/6 (W^{n+1}, stage 1), dt^2/3 (stage 2).
+struct StepTimes {
+  double dt, h, h2, s6, s3;
+  float dtf, hf, h2f, s6f, s3f, pad[3];
+};
+static_assert(sizeof(StepTimes) == 72, "StepTimes layout");
+constexpr int STEP_TIMES_DOUBLES = 9;   // storage of one StepTimes in doubles
+
+__host__ __device__ inline StepTimes step_times(double dt) {
+  StepTimes T;
+  const double dt2 = dt * dt;
+  T.dt = dt; T.h = 0.5 * dt; T.h2 = 0.125 * dt2; T.s6 = dt2 * (1.0 / 6.0); T.s3 = dt2 * (1.0 / 3.0);
+  T.dtf = (float)T.dt; T.hf = (float)T.h; T.h2f = (float)T.h2; T.s6f = (float)T.s6; T.s3f = (float)T.s3;
+  T.pad[0] = T.pad[1] = T.pad[2] = 0.f;
+  return T;
+}
+
 // One face sweep (one direction, one stage).
 struct FaceArgs {
   const double* W;     // [nv][ny][nx] conservative cell averages
@@ -48,6 +67,7 @@ struct FaceArgs32 {
   float dnf, itanf, gammaf, epsf;   // single-precision copies (dn, 1/dtan, gamma, WENO eps)
   int stage;
   PhysParams P;
+  const StepTimes* tc;  // the step's time constants (same storage as dtp)
 };
 
 // FP32-bulk cell update: FP64 accumulation; writes the next mirror.
@@ -76,6 +96,7 @@ cudaError_t launch_update(const UpdateArgs& a, int dim, int stage, cudaStream_t 
 cudaError_t launch_wavespeed(const double* W, int nx, int ny, int dim, double gamma, double dx,
                              double dy, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
+cudaError_t launch_set_times(StepTimes* p, double dt, cudaStream_t s);
 cudaError_t probe_fma(int fp64, int iters, double* flops, cudaStream_t s);
 
 }  // namespace gks

@@ -8,14 +8,12 @@
 // (hi_k - hi_ref) + (lo_k - lo_ref), keep single-precision accuracy relative to the
 // difference.  Slopes are mirrored as floats.
 //
-// A face writes single-precision deltas:
-//   stage 1: comp 0 dF = F - F_Euler(W_ref), comp 1 F_t,
-//            comp 2 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt,
-//            comp 3 dLambda = W0 - W_ref + dt W_t + dt^2/6 W_tt
-//   stage 2: comp 0 F_t*, comp 1 W_tt*
-// and the cell update adds the FP64 reference parts (F_Euler(W_ref), W_ref), so the MSMD
-// accumulation of cell averages and slopes, and conservation, stay in FP64.  The
-// time-integration coefficients of the exponential terms are FP64 (gks_device.cuh).
+// A face evaluates dF = F - F_Euler(W_ref), F_t, W0 - W_ref, W_t and W_tt in single
+// precision and writes its flux parts once, in FP64, with the FP64 reference flux added
+// (write_face32), and its interface-value parts as single-precision deltas from W_ref; the
+// cell update adds W_ref back, so the MSMD accumulation of cell averages and slopes, and
+// conservation, stay in FP64.  The time-integration coefficients of the exponential terms
+// are FP64 (gks_device.cuh).
 #pragma once
 #include "gks_kernels.cuh"
 #include "gks_sweep.cuh"
@@ -35,38 +33,36 @@ template <bool CG>
 __device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
 
 // Face outputs of the FP32-bulk sweeps (face buffer viewed as FP64 planes then FP32 planes):
-//   stage 1: FP64 Phi = dt/2 (F_ref + dF) + dt^2/8 F_t, FP64 Psi = dt (F_ref + dF) + dt^2/6 F_t,
+//   stage 1: FP64 Phi = dt/2 F_ref + (dt/2 dF + dt^2/8 F_t), FP64 Psi = dt F_ref + (dt dF + dt^2/6 F_t),
 //            FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt, FP32 dLambda (dt, dt^2/6)
 //   stage 2: FP64 Theta = dt^2/3 F_t*, FP32 T = dt^2/3 W_tt*
-// F_ref is the FP64 Euler flux of the face's reference cell.  Writing the flux parts once per
-// face in FP64 makes their differences across a cell telescope to FP64 rounding, so the
-// FP64 accumulation of the cell averages conserves exactly.
-template <int DIM>
-__device__ __forceinline__ void write_face32(void* outv, long face, long nfaces, int stage, double dt,
+// F_ref is the FP64 Euler flux of the face's reference cell; the bracketed parts are the
+// single-precision deltas, formed in single precision.  Each flux part is one FP64 value
+// per face, so its differences across a cell telescope to FP64 rounding and the FP64
+// accumulation of the cell averages conserves exactly.  tc: the step's time constants.
+template <int DIM, bool CG>
+__device__ __forceinline__ void write_face32(void* outv, long face, long nfaces, int stage, const StepTimes* tc,
                                              const double* Fref, const float* F, const float* Ft,
                                              const float* dW0, const float* Wt, const float* Wtt) {
   const int N = DIM + 2;
   double* o64 = static_cast<double*>(outv);
   if (stage == 1) {
     float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
-    const double h = 0.5 * dt, h2 = 0.125 * dt * dt, s6 = dt * dt / 6.0;
-    const float hf = (float)h, h2f = (float)h2, dtf = (float)dt, s6f = (float)s6;
+    const double h = ldd<CG>(&tc->h), dt = ldd<CG>(&tc->dt);
+    const float hf = ldf<CG>(&tc->hf), h2f = ldf<CG>(&tc->h2f), dtf = ldf<CG>(&tc->dtf), s6f = ldf<CG>(&tc->s6f);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      double Fv = Fref[v] + (double)F[v];
-      double Ftv = (double)Ft[v];
-      o64[(0L * N + v) * nfaces + face] = h * Fv + h2 * Ftv;
-      o64[(1L * N + v) * nfaces + face] = dt * Fv + s6 * Ftv;
+      o64[(0L * N + v) * nfaces + face] = fma(h, Fref[v], (double)(hf * F[v] + h2f * Ft[v]));
+      o64[(1L * N + v) * nfaces + face] = fma(dt, Fref[v], (double)(dtf * F[v] + s6f * Ft[v]));
       o32[(0L * N + v) * nfaces + face] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
       o32[(1L * N + v) * nfaces + face] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
     }
   } else {
     float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
-    const double s3 = dt * dt / 3.0;
-    const float s3f = (float)s3;
+    const float s3f = ldf<CG>(&tc->s3f);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o64[(0L * N + v) * nfaces + face] = s3 * (double)Ft[v];
+      o64[(0L * N + v) * nfaces + face] = (double)(s3f * Ft[v]);
       o32[v * nfaces + face] = s3f * Wtt[v];
     }
   }
@@ -117,7 +113,7 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
 #pragma unroll
     for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(a.fref + v * ncell + cref);
   }
-  write_face32<1>(a.out, f, a.nx + 1, a.stage, dt, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
+  write_face32<1, CG>(a.out, f, a.nx + 1, a.stage, a.tc, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
 }
 
 template <int ORDER, bool WENO, bool VISC>
@@ -294,12 +290,13 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 #pragma unroll
     for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(fr + v * ncell + cr);
   }
-  write_face32<2>(a.out, face, nfaces, a.stage, dt, Fref, F, Ft, dW0, Wt, Wtt);
+  write_face32<2, CG>(a.out, face, nfaces, a.stage, a.tc, Fref, F, Ft, dW0, Wt, Wtt);
   }
 }
 
+// Linear Euler tiles fit 128 registers without spilling: four blocks (16 warps) per SM.
 template <int ORDER, bool WENO, bool VISC, int DIR>
-__global__ void __launch_bounds__(TA32 * TB32) faces_2d_f32_kernel(FaceArgs32 a) {
+__global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
   sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
 }
@@ -401,9 +398,9 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       const float dOj = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
       const float dLj = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
       const double dW = W - ldd<CG>(a.W + v * ncell + cl);
-      double ws = W - (ldd<CG>(Phi + fxl + 1) - ldd<CG>(Phi + fxl)) * idx;
+      double inc = (ldd<CG>(Phi + fxl + 1) - ldd<CG>(Phi + fxl)) * idx;   // W - W* (flux part)
       double wa = W - (ldd<CG>(Psi + fxl + 1) - ldd<CG>(Psi + fxl)) * idx;
-      accX[v * ncell + c] = (dW + (double)dLj) * idx;
+      accX[v * ncell + c] = fma(dW, idx, (double)(dLj * idxf));
       float wxs = ((float)dW + dOj) * idxf;
       float wys = 0.f;
       if (DIM == 2) {
@@ -412,16 +409,23 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
         const float dOy = ldf<CG>(y32 + (0L * N + v) * nfy + fyt) - ldf<CG>(y32 + (0L * N + v) * nfy + fyb);
         const float dLy = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
         const double dWy = W - ldd<CG>(a.W + v * ncell + cb);
-        ws -= (ldd<CG>(PhiY + fyt) - ldd<CG>(PhiY + fyb)) * idy;
+        inc = fma(ldd<CG>(PhiY + fyt) - ldd<CG>(PhiY + fyb), idy, inc);
         wa -= (ldd<CG>(PsiY + fyt) - ldd<CG>(PsiY + fyb)) * idy;
-        accY[v * ncell + c] = (dWy + (double)dLy) * idy;
+        accY[v * ncell + c] = fma(dWy, idy, (double)(dLy * idyf));
         wys = ((float)dWy + dOy) * idyf;
       }
       accW[v * ncell + c] = wa;
-      // W* only as the FP32 mirror read by the stage-2 sweep
-      const float hi = (float)ws;
+      // W* only as the FP32 mirror read by the stage-2 sweep: this cell's hi/lo mirror of W
+      // plus the single-precision increment, added exactly (two-sum) and renormalised.
+      const float d = -(float)inc;
+      const float h0 = M[v * ncell + c];
+      float lo = M[L + v * ncell + c];
+      const float s1 = h0 + d;
+      const float bb = s1 - h0;
+      lo += (h0 - (s1 - bb)) + (d - bb);
+      const float hi = s1 + lo;
       M[v * ncell + c] = hi;
-      M[L + v * ncell + c] = (float)(ws - (double)hi);
+      M[L + v * ncell + c] = lo - (hi - s1);
       M[2 * L + v * ncell + c] = wxs;
       if (DIM == 2) M[3 * L + v * ncell + c] = wys;
     }

@@ -133,6 +133,13 @@ cudaError_t launch_wavespeed(const double* W, int nx, int ny, int dim, double ga
 
 __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 
+__global__ void set_times_kernel(StepTimes* p, double dt) { *p = step_times(dt); }
+
+cudaError_t launch_set_times(StepTimes* p, double dt, cudaStream_t s) {
+  set_times_kernel<<<1, 1, 0, s>>>(p, dt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s) {
   set_scalar_kernel<<<1, 1, 0, s>>>(p, v);
   return cudaGetLastError();

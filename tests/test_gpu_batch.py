@@ -3,8 +3,10 @@
 A problem advanced in a batch runs the same device code as the same problem advanced alone
 by the FP32-bulk form.  The two are compiled into different kernels, and the compiler's
 choice of fusing a multiply and an add into one FMA depends on the surrounding code, so the
-two agree to single-precision rounding of the FP32 parts (bounds below: W within 1e-7
-relative, slopes within 1e-6 of max|W|/dx), not bitwise.  Within the batch the result does
+two agree to single-precision rounding of the FP32 parts, not bitwise.  At a discontinuity
+the single-precision flux delta is as large as the flux itself, so the differences reach
+~2e-7 of W there (measured on a GB300); the bounds below (W within 1e-6 relative, slopes
+within 1e-5 of max|W|/dx) stay under the FP32-bulk form's own bounds against FP64.  Within the batch the result does
 not depend on the tile shape, the occupancy or the order in which tiles are handed out
 (bitwise).  The autotuner must not change the state; a dependency wait that cannot be
 satisfied must end in GKS_ETIMEOUT, not a hang.
@@ -30,7 +32,7 @@ def mixed_states(n=10, seed=5, n1=(100, 3000), n2=(16, 96)):
     return [inputs.build_problem(s) for s in specs]
 
 
-TOL_W, TOL_SLOPE = 1e-7, 1e-6
+TOL_W, TOL_SLOPE = 1e-6, 1e-5
 
 
 def assert_close_to_alone(got, ref, st, what):
