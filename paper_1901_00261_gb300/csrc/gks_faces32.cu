@@ -32,23 +32,29 @@ cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool vi
   return visc ? launch_1d32_t<8, true, true>(a, s) : launch_1d32_t<8, true, false>(a, s);
 }
 
+// Face rows per thread of the standalone 2D sweep tiles (TA32 x TB32 * SWEEP32_FPT faces).
+#ifndef SWEEP32_FPT
+#define SWEEP32_FPT 2
+#endif
+
 template <int ORDER, bool WENO, bool VISC, int DIR>
 static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
-  typedef Tile32<DIR, 1> T;
+  const int FPT = SWEEP32_FPT;
+  typedef Tile32<DIR, FPT> T;
   const int NQ = WENO ? 7 : 3;
   size_t shmem = sizeof(float) * (NQ + 2) * 4 * T::NS;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR>,
+    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 block(TA32, TB32);
   dim3 grid;
-  if (DIR == 0) grid = dim3((a.nx + 1 + TA32 - 1) / TA32, (a.ny + TB32 - 1) / TB32);
-  else grid = dim3((a.nx + TA32 - 1) / TA32, (a.ny + 1 + TB32 - 1) / TB32);
-  faces_2d_f32_kernel<ORDER, WENO, VISC, DIR><<<grid, block, shmem, s>>>(a);
+  if (DIR == 0) grid = dim3((a.nx + 1 + TA32 - 1) / TA32, (a.ny + T::TB - 1) / T::TB);
+  else grid = dim3((a.nx + TA32 - 1) / TA32, (a.ny + 1 + T::TB - 1) / T::TB);
+  faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,40 @@
 
 namespace gks {
 
+// 1/x for a positive normal x within the float range: a single-precision seed refined by
+// two Newton steps r <- r + r (1 - x r) in FP64 (each squares the relative error, from
+// ~2^-23 to below FP64 rounding).  The reference fluxes only; no IEEE rounding guarantee.
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Split a binary64 value into floats with w = hi + lo + err, |err| <= 2^-47 |w|, on the
+// integer and FP32 pipes: hi is w's significand truncated to 24 bits (a bit copy), lo the
+// remaining 29 fraction bits, built exactly in two parts and rounded once to a float by an
+// FMA, then scaled by a power of two.  Magnitudes outside [2^-74, 2^128) (zero, tiny, huge)
+// take the conversion path.
+__device__ __forceinline__ void split_hilo(double w, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const int e = (int)((bh >> 20) & 0x7ffu);   // biased binary64 exponent
+  if (e >= 949 && e <= 1150) {
+    const unsigned sign = bh & 0x80000000u;
+    hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((bh & 0xfffffu) << 3) | (bl >> 29));
+    const unsigned r = bl & 0x1fffffffu;   // value r * 2^(e - 1075)
+    const float rl = __uint_as_float(0x4b000000u | (r & 0x7fffffu)) - 8388608.0f;   // r mod 2^23, exact
+    const float rh = __uint_as_float(0x4b000000u | (r >> 23)) - 8388608.0f;         // r / 2^23, exact
+    const float rf = fmaf(rh, 8388608.0f, rl);                                     // r rounded to 24 bits
+    lo = __uint_as_float(__float_as_uint(rf * __uint_as_float((unsigned)(e - 948) << 23)) | sign);
+  } else {
+    hi = (float)w;
+    lo = (float)(w - (double)hi);
+  }
+}
+
 template <int DIM>
 __device__ __forceinline__ void swap_uv_f(float* w) {
   if (DIM == 2) { float t = w[1]; w[1] = w[2]; w[2] = t; }
@@ -295,10 +329,10 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 }
 
 // Linear Euler tiles fit 128 registers without spilling: four blocks (16 warps) per SM.
-template <int ORDER, bool WENO, bool VISC, int DIR>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT>
 __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,18 +346,17 @@ __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_
 template <int DIM>
 __device__ __forceinline__ void euler_fluxes64(const double* W, double gamma, double* F, double* G) {
   const int N = DIM + 2;
-  double irho = 1.0 / W[0];
-  double U = W[1] * irho, V = DIM == 2 ? W[2] * irho : 0.0;
-  double p = (gamma - 1.0) * (W[N - 1] - 0.5 * (W[1] * U + (DIM == 2 ? W[2] * V : 0.0)));
-#pragma unroll
-  for (int k = 0; k < N; ++k) F[k] = W[k] * U;
-  F[1] += p;
-  F[N - 1] += p * U;
+  const double irho = rcp64(W[0]);
+  const double U = W[1] * irho, V = DIM == 2 ? W[2] * irho : 0.0;
+  const double p = (gamma - 1.0) * (W[N - 1] - 0.5 * (W[1] * U + (DIM == 2 ? W[2] * V : 0.0)));
+  const double Ep = W[N - 1] + p;
+  F[0] = W[1];
+  F[1] = W[1] * U + p;
+  F[N - 1] = Ep * U;
   if (DIM == 2) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) G[k] = W[k] * V;
-    G[2] += p;
-    G[N - 1] += p * V;
+    const double muv = W[1] * V;   // rho U V
+    F[2] = muv;
+    G[0] = W[2]; G[1] = muv; G[2] = W[2] * V + p; G[3] = Ep * V;
   }
 }
 
@@ -335,9 +368,10 @@ __device__ __forceinline__ void write_mirror(float* M, double* fref, long c, lon
   const long L = N * ncell;
 #pragma unroll
   for (int v = 0; v < N; ++v) {
-    float hi = (float)w[v];
+    float hi, lo;
+    split_hilo(w[v], hi, lo);
     M[v * ncell + c] = hi;
-    M[L + v * ncell + c] = (float)(w[v] - (double)hi);
+    M[L + v * ncell + c] = lo;
     M[2 * L + v * ncell + c] = (float)wx[v];
     if (DIM == 2) M[3 * L + v * ncell + c] = (float)wy[v];
   }
