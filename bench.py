@@ -33,12 +33,74 @@ import numpy as np  # noqa: E402
 METRIC = "cell-updates/s (2D 8th-order GKS, FP32-bulk vs FP64, isentropic vortex)"
 UNIT = "cell-updates/s"
 CFL = 0.3
-# FP64 floating-point operations per face of one face-sweep launch (FMA = 2) of the 2D
-# 8th-order linear Euler sweep, counted by ncu's executed-instruction counters
-# (768.6 DFMA + 243.0 DMUL + 130.0 DADD per face; profiles/faces_2d_vortex_fp64.md).
+# Algorithmic figures per unit of the kernels that can dominate a step (2D, 8th order, linear
+# Euler), stated with their derivation in the design doc:
+#  - FP64 sweep: FP64 flops per face (FMA = 2), from ncu's executed-instruction counters
+#    (768.6 DFMA + 243.0 DMUL + 130.0 DADD per face; profiles/faces_2d_vortex_fp64.md).
+#  - FP32-bulk sweep: FP32 flops per face, from the same counters (profiles/faces_2d_vortex_fp32bulk.md).
+#  - FP32-bulk updates: bytes per cell read and written once (W, own mirror, one x- and one
+#    y-face's flux parts; accumulators, mirror, reference fluxes) and FP64 flops per cell
+#    counted from the source.
 FLOPS_PER_FACE = {("fp64", 8): 1910.2,
-                  # FP32-bulk sweep (x faces, stage 1): 807.2 FFMA + 282.0 FMUL + 326.1 FADD per face
                   ("fp32", 8): 2222.5}
+UPDATE_MODEL = {"update_stage1": {"bytes_per_cell": 416.0, "f64_flops_per_cell": 68.0},
+                "update_stage2": {"bytes_per_cell": 416.0, "f64_flops_per_cell": 64.0}}
+# DRAM bytes (read + write) per cell of one launch, from an ncu capture of the 1024^2 case
+# scaled by the cell count (streaming kernels: traffic grows in proportion); None where no
+# capture of the current kernel exists.
+TRAFFIC_PER_CELL = {}
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """HBM copy bandwidth in GB/s and its source: the measured figure when present."""
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s GB300 copy bandwidth)"
+
+
+def roofline(form, name, ms, nx, ny, order, peak64, peak32):
+    """Roofline of one launch of kernel `name` taking `ms` milliseconds."""
+    ncell = nx * ny
+    src32 = "FP32 FMA-chain probe measured in this run"
+    src64 = "FP64 FMA-chain probe measured in this run"
+    if name.startswith("update"):
+        m = UPDATE_MODEL.get(name) if form == "fp32" else None
+        if m is None:
+            return {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                    "traffic": None, "kernel": name}
+        gbs = m["bytes_per_cell"] * ncell / (ms * 1e-3) / 1e9
+        hpeak, hsrc = hbm_peak()
+        tf = m["f64_flops_per_cell"] * ncell / (ms * 1e-3) / 1e12
+        tr = TRAFFIC_PER_CELL.get((form, name))
+        hbm = {"bound": "hbm", "achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
+               "traffic": None if tr is None else tr * ncell, "kernel": name, "peak_source": hsrc,
+               "algorithmic_bytes_per_cell": m["bytes_per_cell"]}
+        alu = {"bound": "alu", "achieved": tf, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+               "frac": tf * 1e12 / peak64, "kernel": name, "peak_source": src64,
+               "f64_flops_per_cell": m["f64_flops_per_cell"]}
+        main, other = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
+        main = dict(main)
+        if main["bound"] == "alu":
+            main["traffic"] = hbm["traffic"]
+        main["other_bound"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+        return main
+    nfaces = (nx + 1) * ny if name.startswith("x") else nx * (ny + 1)
+    fpf = FLOPS_PER_FACE.get((form, order))
+    peak = peak64 if form == "fp64" else peak32
+    roof = {"bound": "alu", "achieved": None, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "kernel": name, "peak_source": src64 if form == "fp64" else src32}
+    if fpf is not None:
+        achieved = fpf * nfaces / (ms * 1e-3)
+        roof.update(achieved=achieved / 1e12, frac=achieved / peak)
+    tr = TRAFFIC_PER_CELL.get((form, name))
+    if tr is not None:
+        roof["traffic"] = tr * ncell
+    return roof
 
 
 def parse():
@@ -310,15 +372,7 @@ def main():
         per_launch = kernel_ms / args.steps
         k_dom = int(np.argmax(per_launch))
         name = slot_names[k_dom]
-        nfaces = (st.nx + 1) * st.ny if name.startswith("x") else st.nx * (st.ny + 1)
-        fpf = FLOPS_PER_FACE.get((form, args.order))
-        peak = peak64 if form == "fp64" else peak32
-        roof = {"bound": "alu", "achieved": None, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": name,
-                "peak_source": f"{'FP64' if form == 'fp64' else 'FP32'} FMA-chain probe measured in this run"}
-        if fpf is not None and not name.startswith("update"):
-            achieved = fpf * nfaces / (per_launch[k_dom] * 1e-3)
-            roof.update(achieved=achieved / 1e12, frac=achieved / peak)
+        roof = roofline(form, name, float(per_launch[k_dom]), st.nx, st.ny, args.order, peak64, peak32)
         r = {"value": ncell * args.steps * ws / (ms * 1e-3), "ms_per_step": ms / args.steps,
              "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
              "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}

@@ -170,9 +170,8 @@ __global__ void __launch_bounds__(TA32 * TB32) batch_kernel(BatchArgs b) {
 
 template <int CLASS, int FPT>
 size_t batch_smem() {
-  const int nq = CLASS == 0 ? 3 : 7;
-  const int ns0 = Tile32<0, FPT>::NS, ns1 = Tile32<1, FPT>::NS;
-  return sizeof(float) * (nq + 2) * 4 * (ns0 > ns1 ? ns0 : ns1);
+  const size_t s0 = Tile32<0, FPT>::smem_bytes(CLASS != 0), s1 = Tile32<1, FPT>::smem_bytes(CLASS != 0);
+  return s0 > s1 ? s0 : s1;
 }
 
 typedef void (*BatchKernelFn)(BatchArgs);

@@ -41,8 +41,7 @@ template <int ORDER, bool WENO, bool VISC, int DIR>
 static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   const int FPT = SWEEP32_FPT;
   typedef Tile32<DIR, FPT> T;
-  const int NQ = WENO ? 7 : 3;
-  size_t shmem = sizeof(float) * (NQ + 2) * 4 * T::NS;
+  const size_t shmem = T::smem_bytes(WENO);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT>,

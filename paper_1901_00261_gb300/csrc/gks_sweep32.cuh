@@ -66,30 +66,37 @@ __device__ __forceinline__ float ldf(const float* p) { return CG ? __ldcg(p) : *
 template <bool CG>
 __device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
 
-// Face outputs of the FP32-bulk sweeps (face buffer viewed as FP64 planes then FP32 planes):
-//   stage 1: FP64 Phi = dt/2 F_ref + (dt/2 dF + dt^2/8 F_t), FP64 Psi = dt F_ref + (dt dF + dt^2/6 F_t),
-//            FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt, FP32 dLambda (dt, dt^2/6)
+// Face outputs of the FP32-bulk sweeps (face buffer viewed as N FP64 planes, then FP32 planes):
+//   stage 1: FP64 Psi = dt F_ref + (dt dF + dt^2/6 F_t) (the W^{n+1} flux part),
+//            FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt, FP32 dLambda (dt, dt^2/6),
+//            FP32 A = dt/2 dF + dt^2/8 F_t and D = dt/2 (F_Euler(W_right) - F_Euler(W_ref)) - A
 //   stage 2: FP64 Theta = dt^2/3 F_t*, FP32 T = dt^2/3 W_tt*
-// F_ref is the FP64 Euler flux of the face's reference cell; the bracketed parts are the
-// single-precision deltas, formed in single precision.  Each flux part is one FP64 value
-// per face, so its differences across a cell telescope to FP64 rounding and the FP64
-// accumulation of the cell averages conserves exactly.  tc: the step's time constants.
+// F_ref is the FP64 Euler flux of the face's reference (left) cell; the bracketed part of Psi
+// is the single-precision delta.  Psi and Theta are one FP64 value per face, so their
+// differences across a cell telescope to FP64 rounding and the FP64 accumulation of the cell
+// averages conserves exactly.  The dt/2 flux part only moves the intermediate state W*, so it
+// stays in single precision: across cell i its difference is A_{i+1/2} + D_{i-1/2}, with
+// the reference-flux difference dFc = F_Euler(W_right) - F_Euler(W_ref) of the face's two
+// cells in the single-precision delta form.  tc: the step's time constants.
 template <int DIM, bool CG>
 __device__ __forceinline__ void write_face32(void* outv, long face, long nfaces, int stage, const StepTimes* tc,
                                              const double* Fref, const float* F, const float* Ft,
-                                             const float* dW0, const float* Wt, const float* Wtt) {
+                                             const float* dW0, const float* Wt, const float* Wtt,
+                                             const float* dFc) {
   const int N = DIM + 2;
   double* o64 = static_cast<double*>(outv);
   if (stage == 1) {
-    float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
-    const double h = ldd<CG>(&tc->h), dt = ldd<CG>(&tc->dt);
+    float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
+    const double dt = ldd<CG>(&tc->dt);
     const float hf = ldf<CG>(&tc->hf), h2f = ldf<CG>(&tc->h2f), dtf = ldf<CG>(&tc->dtf), s6f = ldf<CG>(&tc->s6f);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o64[(0L * N + v) * nfaces + face] = fma(h, Fref[v], (double)(hf * F[v] + h2f * Ft[v]));
-      o64[(1L * N + v) * nfaces + face] = fma(dt, Fref[v], (double)(dtf * F[v] + s6f * Ft[v]));
+      o64[(long)v * nfaces + face] = fma(dt, Fref[v], (double)(dtf * F[v] + s6f * Ft[v]));
       o32[(0L * N + v) * nfaces + face] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
       o32[(1L * N + v) * nfaces + face] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
+      const float A = hf * F[v] + h2f * Ft[v];
+      o32[(2L * N + v) * nfaces + face] = A;
+      o32[(3L * N + v) * nfaces + face] = hf * dFc[v] - A;
     }
   } else {
     float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
@@ -127,6 +134,9 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
     }
   }
   float rec[WENO ? 7 : 3][N];
+  float dr[N];   // W_right - W_ref
+#pragma unroll
+  for (int v = 0; v < N; ++v) dr[v] = in[v][2];
   normal_recon<float, 1, ORDER, WENO>(in, a.dnf, a.gammaf, a.epsf, rec, ref);
   PointIn<float, 1> pin;
   float d0[N];
@@ -147,7 +157,9 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
 #pragma unroll
     for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(a.fref + v * ncell + cref);
   }
-  write_face32<1, CG>(a.out, f, a.nx + 1, a.stage, a.tc, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
+  float dFc[N] = {0.f, 0.f, 0.f};
+  if (a.stage == 1) euler_flux_delta<float, 1>(ref, dr, a.gammaf, dFc);
+  write_face32<1, CG>(a.out, f, a.nx + 1, a.stage, a.tc, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
 }
 
 template <int ORDER, bool WENO, bool VISC>
@@ -170,6 +182,9 @@ struct Tile32 {
   static constexpr int SA = DIR == 0 ? TA32 : TA32 + 4;
   static constexpr int SB = DIR == 0 ? TB + 4 : TB;
   static constexpr int NS = SA * SB;
+  // shared memory: NQ reconstructed quantities, the reference (hi, lo) and the reference-flux
+  // difference of the face's two cells, 4 variables each, per slot
+  static constexpr size_t smem_bytes(bool weno) { return sizeof(float) * ((weno ? 7 : 3) + 3) * 4 * NS; }
 };
 
 // One tile of TA32 x TB32 faces; tid = linear thread index in a block of TA32 * TB32 threads;
@@ -183,6 +198,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   const int tx = tid % TA32, ty = tid / TA32;
   float* sref = smf + NQ * N * T::NS;
   float* sreflo = sref + N * T::NS;
+  float* sdfc = sreflo + N * T::NS;
   const double dt = ldd<CG>(a.dtp);
   const long ncell = (long)a.nx * a.ny;
   const long L = N * ncell;
@@ -195,7 +211,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
     if (DIR == 0) { fn = bx * TA32 + sa; ct = map_index(by * T::TB + sb - 2, a.ny, a.bcy); }
     else { ct = map_index(bx * TA32 + sa - 2, a.nx, a.bcx); fn = by * T::TB + sb; }
     float rec[NQ][N];
-    float ref[N], rlo[N];
+    float ref[N], rlo[N], dfc[N] = {0.f, 0.f, 0.f, 0.f};
     if (fn < nn) {
       long cr;
       if (DIR == 0) cr = (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx);
@@ -221,7 +237,12 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
           in[v][4 + o] = a.dnf * g[v];
         }
       }
+      float dr[N];   // W_right - W_ref
+#pragma unroll
+      for (int v = 0; v < N; ++v) dr[v] = in[v][2];
       normal_recon<float, 2, ORDER, WENO>(in, a.dnf, a.gammaf, a.epsf, rec, ref);
+      // F_Euler(W_right) - F_Euler(W_ref) of the face's two cells, in the face's frame
+      if (a.stage == 1) euler_flux_delta<float, 2>(ref, dr, a.gammaf, dfc);
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q)
@@ -235,7 +256,9 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 #pragma unroll
       for (int v = 0; v < N; ++v) smf[(q * N + v) * T::NS + s] = rec[q][v];
 #pragma unroll
-    for (int v = 0; v < N; ++v) { sref[v * T::NS + s] = ref[v]; sreflo[v * T::NS + s] = rlo[v]; }
+    for (int v = 0; v < N; ++v) {
+      sref[v * T::NS + s] = ref[v]; sreflo[v * T::NS + s] = rlo[v]; sdfc[v * T::NS + s] = dfc[v];
+    }
   }
   __syncthreads();
 
@@ -311,7 +334,12 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
     }
   }
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
-  if (DIR == 1) { swap_uv_f<2>(F); swap_uv_f<2>(Ft); swap_uv_f<2>(dW0); swap_uv_f<2>(Wt); swap_uv_f<2>(Wtt); }
+  float dFc[N];   // reference-flux difference of the face's two cells (stage 1; phase A)
+#pragma unroll
+  for (int v = 0; v < N; ++v) dFc[v] = sdfc[v * T::NS + slot[2]];
+  if (DIR == 1) {
+    swap_uv_f<2>(F); swap_uv_f<2>(Ft); swap_uv_f<2>(dW0); swap_uv_f<2>(Wt); swap_uv_f<2>(Wtt); swap_uv_f<2>(dFc);
+  }
   long face, nfaces;
   if (DIR == 0) { face = (long)ct * (a.nx + 1) + fn; nfaces = (long)a.ny * (a.nx + 1); }
   else { face = (long)fn * a.nx + ct; nfaces = (long)(a.ny + 1) * a.nx; }
@@ -324,7 +352,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 #pragma unroll
     for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(fr + v * ncell + cr);
   }
-  write_face32<2, CG>(a.out, face, nfaces, a.stage, a.tc, Fref, F, Ft, dW0, Wt, Wtt);
+  write_face32<2, CG>(a.out, face, nfaces, a.stage, a.tc, Fref, F, Ft, dW0, Wt, Wtt, dFc);
   }
 }
 
@@ -418,8 +446,8 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   const double* y64 = reinterpret_cast<const double*>(a.fy);
   const double idx = a.idx, idy = a.idy;
   if (STAGE == 1) {
-    const float* x32 = reinterpret_cast<const float*>(x64 + 2L * N * nfx);
-    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 2L * N * nfy) : nullptr;
+    const float* x32 = reinterpret_cast<const float*>(x64 + 1L * N * nfx);
+    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 1L * N * nfy) : nullptr;
     const long cl = (long)j * a.nx + map_index(i - 1, a.nx, a.bcx);
     const long cb = DIM == 2 ? (long)map_index(j - 1, a.ny, a.bcy) * a.nx + i : 0;
     const float idxf = (float)idx, idyf = (float)idy;
@@ -427,23 +455,22 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       const double W = ldd<CG>(a.W + v * ncell + c);
-      const double* Phi = x64 + (0L * N + v) * nfx;
-      const double* Psi = x64 + (1L * N + v) * nfx;
+      const double* Psi = x64 + (long)v * nfx;
       const float dOj = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
       const float dLj = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
+      // W - W* (flux part), single precision: (A_{i+1/2} + D_{i-1/2}) / dx
+      float inc = (ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1) + ldf<CG>(x32 + (3L * N + v) * nfx + fxl)) * idxf;
       const double dW = W - ldd<CG>(a.W + v * ncell + cl);
-      double inc = (ldd<CG>(Phi + fxl + 1) - ldd<CG>(Phi + fxl)) * idx;   // W - W* (flux part)
       double wa = W - (ldd<CG>(Psi + fxl + 1) - ldd<CG>(Psi + fxl)) * idx;
       accX[v * ncell + c] = fma(dW, idx, (double)(dLj * idxf));
       float wxs = ((float)dW + dOj) * idxf;
       float wys = 0.f;
       if (DIM == 2) {
-        const double* PhiY = y64 + (0L * N + v) * nfy;
-        const double* PsiY = y64 + (1L * N + v) * nfy;
+        const double* PsiY = y64 + (long)v * nfy;
         const float dOy = ldf<CG>(y32 + (0L * N + v) * nfy + fyt) - ldf<CG>(y32 + (0L * N + v) * nfy + fyb);
         const float dLy = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
+        inc += (ldf<CG>(y32 + (2L * N + v) * nfy + fyt) + ldf<CG>(y32 + (3L * N + v) * nfy + fyb)) * idyf;
         const double dWy = W - ldd<CG>(a.W + v * ncell + cb);
-        inc = fma(ldd<CG>(PhiY + fyt) - ldd<CG>(PhiY + fyb), idy, inc);
         wa -= (ldd<CG>(PsiY + fyt) - ldd<CG>(PsiY + fyb)) * idy;
         accY[v * ncell + c] = fma(dWy, idy, (double)(dLy * idyf));
         wys = ((float)dWy + dOy) * idyf;
@@ -451,7 +478,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       accW[v * ncell + c] = wa;
       // W* only as the FP32 mirror read by the stage-2 sweep: this cell's hi/lo mirror of W
       // plus the single-precision increment, added exactly (two-sum) and renormalised.
-      const float d = -(float)inc;
+      const float d = -inc;
       const float h0 = M[v * ncell + c];
       float lo = M[L + v * ncell + c];
       const float s1 = h0 + d;
