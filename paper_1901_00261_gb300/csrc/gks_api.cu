@@ -45,7 +45,6 @@ struct gks_ctx {
   double* fy = nullptr;      // y-face buffer [4][nv][ny+1][nx]
   double* d_dt = nullptr;
   float* mirror = nullptr;   // FP32-bulk: [hi | lo | Wx | Wy] floats
-  double* fref = nullptr;    // FP32-bulk: per-cell Euler fluxes [F | G] of the state
   unsigned int* d_status = nullptr;
   unsigned long long* d_ws = nullptr;
   double last_dt = -1.0;
@@ -74,14 +73,14 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
     fa.P = c->P;
     fa.M = c->mirror;
-    fa.fref = c->fref;
+    fa.W = c->state;
     fa.dnf = (float)c->dx; fa.gammaf = (float)c->P.gamma; fa.epsf = (float)c->P.weno_eps;
     const bool visc = c->P.mu > 0.0;
     gks::UpdateArgs32 ua;
     ua.fx = reinterpret_cast<const float*>(c->fx); ua.fy = reinterpret_cast<const float*>(c->fy);
-    ua.acc = c->acc; ua.M = c->mirror; ua.fref = c->fref; ua.dtp = c->d_dt;
+    ua.W = c->state; ua.M = c->mirror;
     ua.nx = c->nx; ua.ny = c->ny; ua.bcx = c->o.bc_x; ua.bcy = c->o.bc_y;
-    ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy; ua.gamma = c->P.gamma;
+    ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy;
     for (int stage = 1; stage <= 2; ++stage) {
       fa.stage = stage;
       fa.Mn = c->mirror + 2 * L; fa.out = c->fx; fa.dn = c->dx; fa.dtan = c->dy;
@@ -99,8 +98,6 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
         mark(false);
         if (e != cudaSuccess) return cuda_fail(e, "y-face sweep (fp32)");
       }
-      ua.W = c->state;
-      ua.Ws = c->state;   // written by stage 2 only
       mark(true);
       e = gks::launch_update32(ua, c->dim, stage, c->stream);
       mark(false);
@@ -148,7 +145,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
 // FP32-bulk: rebuild the float mirror after the FP64 state was replaced.
 int refresh_mirror(gks_ctx* c) {
   if (c->o.precision != GKS_PREC_FP32_BULK) return GKS_OK;
-  cudaError_t e = gks::launch_mirror_ref(c->state, c->mirror, c->fref, c->nx, c->ny, c->dim, c->P.gamma, c->stream);
+  cudaError_t e = gks::launch_mirror(c->state, c->mirror, c->nx, c->ny, c->dim, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mirror");
   return GKS_OK;
 }
@@ -221,8 +218,11 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   const int nsets = c->dim + 1;   // W, Wx (, Wy)
   size_t fxn = (size_t)4 * c->nv * ny * (nx + 1);
   size_t fyn = c->dim == 2 ? (size_t)4 * c->nv * (ny + 1) * nx : 0;
+  // the FP64 form keeps W* and the MSMD accumulators; the FP32-bulk form folds both stages
+  // into the face data and keeps only the state and its float mirror
+  const size_t nstage = o.precision == GKS_PREC_FP64 ? (size_t)nsets * L : 0;
   struct { double** p; size_t n; } bufs[] = {
-      {&c->state, (size_t)nsets * L}, {&c->stage, (size_t)nsets * L}, {&c->acc, (size_t)nsets * L},
+      {&c->state, (size_t)nsets * L}, {&c->stage, nstage}, {&c->acc, nstage},
       {&c->fx, fxn}, {&c->fy, fyn}, {&c->d_dt, (size_t)gks::STEP_TIMES_DOUBLES}};
   for (auto& b : bufs) {
     if (b.n == 0) continue;
@@ -231,7 +231,6 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   }
   if (o.precision == GKS_PREC_FP32_BULK) {
     e = cudaMalloc((void**)&c->mirror, (size_t)(c->dim + 2) * L * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fref, (size_t)c->dim * L * sizeof(double));
     if (e != cudaSuccess) { cuda_fail(e, "device allocation"); gks_destroy(c); return nullptr; }
   }
   e = cudaMalloc((void**)&c->d_status, sizeof(unsigned int));
@@ -410,7 +409,6 @@ void gks_destroy(gks_ctx* c) {
   for (double* b : bufs) if (b) cudaFree(b);
   if (c->d_status) cudaFree(c->d_status);
   if (c->mirror) cudaFree(c->mirror);
-  if (c->fref) cudaFree(c->fref);
   if (c->d_ws) cudaFree(c->d_ws);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

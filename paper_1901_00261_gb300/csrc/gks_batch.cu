@@ -369,7 +369,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
   B->state_off.resize(n);
   B->last_dt.assign(n, -1.0);
   // validate and lay out the arena
-  std::vector<size_t> off_state(n), off_acc(n), off_mir(n), off_fref(n), off_fx(n), off_fy(n);
+  std::vector<size_t> off_state(n), off_mir(n), off_fx(n), off_fy(n);
   size_t bytes = 0;
   B->cls = 0;
   for (int p = 0; p < n; ++p) {
@@ -386,9 +386,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     B->ncell[p] = nc;
     const long L = N * nc;
     off_state[p] = bytes; bytes = align256(bytes + sizeof(double) * (dim + 1) * L);
-    off_acc[p] = bytes; bytes = align256(bytes + sizeof(double) * (dim + 1) * L);
     off_mir[p] = bytes; bytes = align256(bytes + sizeof(float) * (dim + 2) * L);
-    off_fref[p] = bytes; bytes = align256(bytes + sizeof(double) * dim * L);
     off_fx[p] = bytes; bytes = align256(bytes + sizeof(double) * 4 * N * q.ny * (q.nx + 1));
     off_fy[p] = bytes; if (dim == 2) bytes = align256(bytes + sizeof(double) * 4 * N * (q.ny + 1) * q.nx);
   }
@@ -414,9 +412,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     const int dim = q.ny > 1 ? 2 : 1, N = dim + 2;
     const long nc = B->ncell[p], L = N * nc;
     double* state = reinterpret_cast<double*>(B->arena + off_state[p]);
-    double* acc = reinterpret_cast<double*>(B->arena + off_acc[p]);
     float* mir = reinterpret_cast<float*>(B->arena + off_mir[p]);
-    double* fref = reinterpret_cast<double*>(B->arena + off_fref[p]);
     double* fx = reinterpret_cast<double*>(B->arena + off_fx[p]);
     double* fy = dim == 2 ? reinterpret_cast<double*>(B->arena + off_fy[p]) : nullptr;
     B->state_off[p] = (long)(off_state[p] / sizeof(double));
@@ -432,7 +428,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     for (int st = 0; st < 2; ++st) {
       for (int d = 0; d < 2; ++d) {
         gks::FaceArgs32& a = d == 0 ? P.ax[st] : P.ay[st];
-        a.M = mir; a.fref = fref;
+        a.M = mir; a.W = state;
         a.Mn = mir + (2 + d) * L;
         a.out = d == 0 ? (void*)fx : (void*)fy;
         a.dtp = B->ddt + (size_t)gks::STEP_TIMES_DOUBLES * p;   // this problem's step constants
@@ -448,9 +444,9 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     }
     gks::UpdateArgs32& u = P.up;
     u.W = state; u.fx = reinterpret_cast<const float*>(fx); u.fy = reinterpret_cast<const float*>(fy);
-    u.Ws = state; u.acc = acc; u.M = mir; u.fref = fref; u.dtp = B->ddt + (size_t)gks::STEP_TIMES_DOUBLES * p;
+    u.M = mir;
     u.nx = q.nx; u.ny = q.ny; u.bcx = q.bc_x; u.bcy = q.bc_y;
-    u.idx = 1.0 / dx; u.idy = 1.0 / dy; u.gamma = q.gamma;
+    u.idx = 1.0 / dx; u.idy = 1.0 / dy;
     P.tbx_x = (q.nx + 1 + gks::TA32 - 1) / gks::TA32;
     P.tbx_y = (q.nx + gks::TA32 - 1) / gks::TA32;
   }
@@ -503,7 +499,7 @@ int gks_batch_set_state(gks_batch* B, int i, const double* W, const double* Wx, 
     e = cudaMemcpyAsync(state + k * L, src[k], L * sizeof(double), cudaMemcpyHostToDevice, B->stream);
   if (e != cudaSuccess) return bcuda(e, "batch set_state");
   const gks::BatchProblem& P = B->hp[i];
-  e = gks::launch_mirror_ref(state, P.up.M, P.up.fref, q.nx, q.ny, dim, q.gamma, B->stream);
+  e = gks::launch_mirror(state, P.up.M, q.nx, q.ny, dim, B->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B->dstatus + 1 + i, 0, sizeof(unsigned), B->stream);   // a new state: no longer frozen
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   if (e != cudaSuccess) return bcuda(e, "batch set_state");

@@ -3,12 +3,11 @@
 
 namespace gks {
 
-cudaError_t launch_mirror_ref(const double* S, float* M, double* fref, int nx, int ny, int dim,
-                              double gamma, cudaStream_t s) {
+cudaError_t launch_mirror(const double* S, float* M, int nx, int ny, int dim, cudaStream_t s) {
   long ncell = (long)nx * ny;
   unsigned blocks = (unsigned)((ncell + 255) / 256);
-  if (dim == 1) mirror_ref_kernel<1><<<blocks, 256, 0, s>>>(S, M, fref, ncell, gamma);
-  else mirror_ref_kernel<2><<<blocks, 256, 0, s>>>(S, M, fref, ncell, gamma);
+  if (dim == 1) mirror_kernel<1><<<blocks, 256, 0, s>>>(S, M, ncell);
+  else mirror_kernel<2><<<blocks, 256, 0, s>>>(S, M, ncell);
   return cudaGetLastError();
 }
 

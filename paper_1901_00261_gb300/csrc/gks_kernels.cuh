@@ -58,7 +58,7 @@ struct UpdateArgs {
 struct FaceArgs32 {
   const float* M;      // mirror [hi (nv planes) | lo (nv planes) | ...]
   const float* Mn;     // mirrored gradient along the face normal [nv][ny][nx]
-  const double* fref;  // per-cell FP64 Euler fluxes [F | G][nv][ncell]
+  const double* W;     // FP64 state [nv][ny][nx] (stage 1: reference fluxes and cell differences)
   void* out;           // face buffer (FP64 planes, then FP32 planes)
   const double* dtp;
   unsigned int* status;
@@ -72,21 +72,16 @@ struct FaceArgs32 {
 
 // FP32-bulk cell update: FP64 accumulation; writes the next mirror.
 struct UpdateArgs32 {
-  const double* W;     // FP64 state W^n (stage 1)
-  const float* fx;
-  const float* fy;
-  double* Ws;
-  double* acc;
-  float* M;            // mirror written for the next sweep
-  double* fref;        // per-cell FP64 Euler fluxes [F | G][nv][ncell] of the step's state
-  const double* dtp;
+  double* W;           // FP64 state [W | Wx (| Wy)][nv][ny][nx]: W^n read and W^{n+1} written (stage 2)
+  const float* fx;     // x-face buffer (FP64 planes, then FP32 planes; see write_face32)
+  const float* fy;     // y-face buffer (2D)
+  float* M;            // FP32 mirror: W^n / W* / W^{n+1} (hi, lo, Wx, Wy planes)
   int nx, ny, bcx, bcy;
-  double idx, idy, gamma;
+  double idx, idy;
 };
 
 // launchers (defined in the .cu units)
-cudaError_t launch_mirror_ref(const double* S, float* M, double* fref, int nx, int ny, int dim,
-                              double gamma, cudaStream_t s);
+cudaError_t launch_mirror(const double* S, float* M, int nx, int ny, int dim, cudaStream_t s);
 cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_update32(const UpdateArgs32& a, int dim, int stage, cudaStream_t s);

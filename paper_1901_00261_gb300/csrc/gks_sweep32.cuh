@@ -54,6 +54,35 @@ __device__ __forceinline__ void split_hilo(double w, float& hi, float& lo) {
   }
 }
 
+// Prefetch of a global line the face epilogue will read (no register is held meanwhile).
+// CG (persistent batch kernel): into L2, which is coherent for data written earlier in the
+// launch by other SMs; otherwise into L1 (a new launch does not see stale L1 lines).
+template <bool CG>
+__device__ __forceinline__ void prefetch_line(const void* p) {
+  if (CG) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  else asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Start the epilogue's global reads of face `face` (stage 1: the FP64 states of its cells
+// cl, cr; stage 2: its FP64 flux part Xi and FP32 dLT) while the face is evaluated.
+template <int DIM, bool CG>
+__device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, long face, long nfaces, long cl, long cr) {
+  const int N = DIM + 2;
+  const long ncell = (long)a.nx * a.ny;
+  if (a.stage == 1) {
+#pragma unroll
+    for (int v = 0; v < N; ++v) { prefetch_line<CG>(a.W + v * ncell + cl); prefetch_line<CG>(a.W + v * ncell + cr); }
+  } else {
+    const double* o64 = static_cast<const double*>(a.out);
+    const float* o32 = reinterpret_cast<const float*>(o64 + 2L * N * nfaces);
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      prefetch_line<CG>(o64 + (long)v * nfaces + face);
+      prefetch_line<CG>(o32 + (1L * N + v) * nfaces + face);
+    }
+  }
+}
+
 template <int DIM>
 __device__ __forceinline__ void swap_uv_f(float* w) {
   if (DIM == 2) { float t = w[1]; w[1] = w[2]; w[2] = t; }
@@ -66,45 +95,72 @@ __device__ __forceinline__ float ldf(const float* p) { return CG ? __ldcg(p) : *
 template <bool CG>
 __device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
 
-// Face outputs of the FP32-bulk sweeps (face buffer viewed as N FP64 planes, then FP32 planes):
-//   stage 1: FP64 Psi = dt F_ref + (dt dF + dt^2/6 F_t) (the W^{n+1} flux part),
-//            FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt, FP32 dLambda (dt, dt^2/6),
-//            FP32 A = dt/2 dF + dt^2/8 F_t and D = dt/2 (F_Euler(W_right) - F_Euler(W_ref)) - A
-//   stage 2: FP64 Theta = dt^2/3 F_t*, FP32 T = dt^2/3 W_tt*
-// F_ref is the FP64 Euler flux of the face's reference (left) cell; the bracketed part of Psi
-// is the single-precision delta.  Psi and Theta are one FP64 value per face, so their
-// differences across a cell telescope to FP64 rounding and the FP64 accumulation of the cell
-// averages conserves exactly.  The dt/2 flux part only moves the intermediate state W*, so it
-// stays in single precision: across cell i its difference is A_{i+1/2} + D_{i-1/2}, with
-// the reference-flux difference dFc = F_Euler(W_right) - F_Euler(W_ref) of the face's two
-// cells in the single-precision delta form.  tc: the step's time constants.
-template <int DIM, bool CG>
-__device__ __forceinline__ void write_face32(void* outv, long face, long nfaces, int stage, const StepTimes* tc,
-                                             const double* Fref, const float* F, const float* Ft,
-                                             const float* dW0, const float* Wt, const float* Wtt,
-                                             const float* dFc) {
+// Normal Euler flux (global frame) of an FP64 state across a face of direction DIR.
+template <int DIM, int DIR>
+__device__ __forceinline__ void euler_flux64(const double* W, double gamma, double* F) {
   const int N = DIM + 2;
-  double* o64 = static_cast<double*>(outv);
-  if (stage == 1) {
-    float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
-    const double dt = ldd<CG>(&tc->dt);
+  const double irho = rcp64(W[0]);
+  const double U = W[1] * irho, V = DIM == 2 ? W[2] * irho : 0.0;
+  const double p = (gamma - 1.0) * (W[N - 1] - 0.5 * (W[1] * U + (DIM == 2 ? W[2] * V : 0.0)));
+  const double un = DIR == 0 ? U : V;
+  F[0] = W[1 + DIR];
+  F[1] = DIR == 0 ? W[1] * un + p : W[1] * un;
+  if (DIM == 2) F[2] = DIR == 1 ? W[2] * un + p : W[2] * un;
+  F[N - 1] = (W[N - 1] + p) * un;
+}
+
+// Face outputs of the FP32-bulk sweeps.  The face buffer holds 2N FP64 planes, then FP32 planes:
+//   FP64 Xi  = dt F_ref + (dt dF + dt^2/6 F_t)           (stage 1; stage 2 adds dt^2/3 F_t*)
+//   FP64 dW  = W_right - W_left of the face's two cells    (stage 1)
+//   FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt     (stage 1)
+//   FP32 dLT = W0 - W_ref + dt W_t + dt^2/6 W_tt          (stage 1; stage 2 adds dt^2/3 W_tt*)
+//   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1)
+// F_ref = F_Euler(W_left) in FP64 (W_ref = W_left is the face's reference state), dF and F_t the
+// single-precision flux delta and derivative, dFc = F_Euler(W_right) - F_Euler(W_left) in the
+// single-precision delta form.  Xi is one FP64 value per face, so its differences across a
+// cell telescope to FP64 rounding and the FP64 update of the cell averages conserves
+// exactly.  The dt/2 flux part only moves the intermediate state W*, so it stays in single
+// precision: across cell i its difference is A_{i+1/2} + D_{i-1/2}.  F, Ft, dW0, Wt, Wtt,
+// dFc in the global frame; cl, cr: the face's left and right cells.
+template <int DIM, int DIR, bool CG>
+__device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, long nfaces, long cl, long cr,
+                                             const float* F, const float* Ft, const float* dW0,
+                                             const float* Wt, const float* Wtt, const float* dFc) {
+  const int N = DIM + 2;
+  const long ncell = (long)a.nx * a.ny;
+  double* o64 = static_cast<double*>(a.out);
+  float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
+  const StepTimes* tc = a.tc;
+  if (a.stage == 1) {
     const float hf = ldf<CG>(&tc->hf), h2f = ldf<CG>(&tc->h2f), dtf = ldf<CG>(&tc->dtf), s6f = ldf<CG>(&tc->s6f);
+    float dpsi[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o64[(long)v * nfaces + face] = fma(dt, Fref[v], (double)(dtf * F[v] + s6f * Ft[v]));
       o32[(0L * N + v) * nfaces + face] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
       o32[(1L * N + v) * nfaces + face] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
       const float A = hf * F[v] + h2f * Ft[v];
       o32[(2L * N + v) * nfaces + face] = A;
       o32[(3L * N + v) * nfaces + face] = hf * dFc[v] - A;
+      dpsi[v] = dtf * F[v] + s6f * Ft[v];
+    }
+    double wl[N], wr[N], Fref[N];
+#pragma unroll
+    for (int v = 0; v < N; ++v) { wl[v] = ldd<CG>(a.W + v * ncell + cl); wr[v] = ldd<CG>(a.W + v * ncell + cr); }
+    euler_flux64<DIM, DIR>(wl, a.P.gamma, Fref);
+    const double dt = ldd<CG>(&tc->dt);
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      o64[(long)v * nfaces + face] = fma(dt, Fref[v], (double)dpsi[v]);
+      o64[(long)(N + v) * nfaces + face] = wr[v] - wl[v];
     }
   } else {
-    float* o32 = reinterpret_cast<float*>(o64 + 1L * N * nfaces);
     const float s3f = ldf<CG>(&tc->s3f);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o64[(0L * N + v) * nfaces + face] = (double)(s3f * Ft[v]);
-      o32[v * nfaces + face] = s3f * Wtt[v];
+      double* xi = o64 + (long)v * nfaces + face;
+      *xi = ldd<CG>(xi) + (double)(s3f * Ft[v]);
+      float* lt = o32 + (1L * N + v) * nfaces + face;
+      *lt = ldf<CG>(lt) + s3f * Wtt[v];
     }
   }
 }
@@ -116,6 +172,7 @@ template <int ORDER, bool WENO, bool VISC, bool CG>
 __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
   const int N = 3;
   if (f > a.nx) return;
+  prefetch_face_epilogue<1, CG>(a, f, a.nx + 1, map_index(f - 1, a.nx, a.bcx), map_index(f, a.nx, a.bcx));
   const double dt = ldd<CG>(a.dtp);
   const long ncell = a.nx;
   const long L = N * ncell;
@@ -152,14 +209,9 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
   PointOut<float, 1> po;
   bool ok = gks_point<float, 1, WENO, VISC, true>(a.P, pin, dt, po, ref, d0);
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
-  double Fref[N] = {0.0, 0.0, 0.0};
-  if (a.stage == 1) {
-#pragma unroll
-    for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(a.fref + v * ncell + cref);
-  }
   float dFc[N] = {0.f, 0.f, 0.f};
   if (a.stage == 1) euler_flux_delta<float, 1>(ref, dr, a.gammaf, dFc);
-  write_face32<1, CG>(a.out, f, a.nx + 1, a.stage, a.tc, Fref, po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
+  write_face32<1, 0, CG>(a, f, a.nx + 1, cref, map_index(f, a.nx, a.bcx), po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
 }
 
 template <int ORDER, bool WENO, bool VISC>
@@ -270,6 +322,15 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   else { ct = bx * TA32 + tx; fn = by * T::TB + ry; }
   const int nt = DIR == 0 ? a.ny : a.nx;
   if (fn >= nn || ct >= nt) continue;
+  {
+    const long pf = DIR == 0 ? (long)ct * (a.nx + 1) + fn : (long)fn * a.nx + ct;
+    const long pn = DIR == 0 ? (long)a.ny * (a.nx + 1) : (long)(a.ny + 1) * a.nx;
+    const long pl = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
+                             : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
+    const long pr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
+                             : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
+    prefetch_face_epilogue<2, CG>(a, pf, pn, pl, pr);
+  }
   int slot[5];
 #pragma unroll
   for (int t = 0; t < 5; ++t)
@@ -343,16 +404,12 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   long face, nfaces;
   if (DIR == 0) { face = (long)ct * (a.nx + 1) + fn; nfaces = (long)a.ny * (a.nx + 1); }
   else { face = (long)fn * a.nx + ct; nfaces = (long)(a.ny + 1) * a.nx; }
-  double Fref[N] = {0.0, 0.0, 0.0, 0.0};
-  if (a.stage == 1) {
-    // reference cell of the face (global frame): F for x faces, G for y faces
-    long cr = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
-                       : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
-    const double* fr = a.fref + (DIR == 0 ? 0 : L);
-#pragma unroll
-    for (int v = 0; v < N; ++v) Fref[v] = ldd<CG>(fr + v * ncell + cr);
-  }
-  write_face32<2, CG>(a.out, face, nfaces, a.stage, a.tc, Fref, F, Ft, dW0, Wt, Wtt, dFc);
+  // the face's left (reference) and right cells
+  const long cl = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
+                           : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
+  const long cr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
+                           : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
+  write_face32<2, DIR, CG>(a, face, nfaces, cl, cr, F, Ft, dW0, Wt, Wtt, dFc);
   }
 }
 
@@ -364,34 +421,20 @@ __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_
 }
 
 // ---------------------------------------------------------------------------
-// FP32-bulk cell updates.  Face f's reference is cell f-1 (mapped), the left (x) or lower
-// (y) neighbour; the update adds back the reference flux F_Euler(W_ref), kept per cell in
-// FP64 (written when the state is produced), and W_ref for the interface values.
-// Stage 1 accumulates the W^{n+1} and slope parts in FP64 and writes W* only as the FP32
-// mirror read by the stage-2 sweep; stage 2 writes the FP64 state, its mirror and its
-// reference fluxes.
+// FP32-bulk cell updates (face data as written by write_face32; face i of a row is the left
+// face of cell i, its left cell the mapped cell i-1).
+//   Stage 1: W* only as the FP32 mirror read by the stage-2 sweep: this cell's hi/lo mirror
+//     of W^n plus the single-precision increment -(A_{i+1/2} + D_{i-1/2})/dx - (..)/dy, added
+//     exactly (two-sum) and renormalised; the W* slopes (dW + dOmega_{i+1/2} - dOmega_{i-1/2})/dx
+//     as floats.
+//   Stage 2: W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
+//     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
+//     place (each cell reads only its own state), and the mirror of W^{n+1}.
 // ---------------------------------------------------------------------------
+// FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
 template <int DIM>
-__device__ __forceinline__ void euler_fluxes64(const double* W, double gamma, double* F, double* G) {
-  const int N = DIM + 2;
-  const double irho = rcp64(W[0]);
-  const double U = W[1] * irho, V = DIM == 2 ? W[2] * irho : 0.0;
-  const double p = (gamma - 1.0) * (W[N - 1] - 0.5 * (W[1] * U + (DIM == 2 ? W[2] * V : 0.0)));
-  const double Ep = W[N - 1] + p;
-  F[0] = W[1];
-  F[1] = W[1] * U + p;
-  F[N - 1] = Ep * U;
-  if (DIM == 2) {
-    const double muv = W[1] * V;   // rho U V
-    F[2] = muv;
-    G[0] = W[2]; G[1] = muv; G[2] = W[2] * V + p; G[3] = Ep * V;
-  }
-}
-
-// FP32 mirror and reference fluxes of one cell's FP64 state.
-template <int DIM>
-__device__ __forceinline__ void write_mirror(float* M, double* fref, long c, long ncell, const double* w,
-                                             const double* wx, const double* wy, double gamma) {
+__device__ __forceinline__ void write_mirror(float* M, long c, long ncell, const double* w,
+                                             const double* wx, const double* wy) {
   const int N = DIM + 2;
   const long L = N * ncell;
 #pragma unroll
@@ -403,18 +446,10 @@ __device__ __forceinline__ void write_mirror(float* M, double* fref, long c, lon
     M[2 * L + v * ncell + c] = (float)wx[v];
     if (DIM == 2) M[3 * L + v * ncell + c] = (float)wy[v];
   }
-  double F[N], G[N];
-  euler_fluxes64<DIM>(w, gamma, F, G);
-#pragma unroll
-  for (int v = 0; v < N; ++v) {
-    fref[v * ncell + c] = F[v];
-    if (DIM == 2) fref[L + v * ncell + c] = G[v];
-  }
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) mirror_ref_kernel(const double* S, float* M, double* fref,
-                                                         long ncell, double gamma) {
+__global__ void __launch_bounds__(256) mirror_kernel(const double* S, float* M, long ncell) {
   const int N = DIM + 2;
   long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -426,9 +461,8 @@ __global__ void __launch_bounds__(256) mirror_ref_kernel(const double* S, float*
     wx[v] = S[L + v * ncell + c];
     wy[v] = DIM == 2 ? S[2 * L + v * ncell + c] : 0.0;
   }
-  write_mirror<DIM>(M, fref, c, ncell, w, wx, wy, gamma);
+  write_mirror<DIM>(M, c, ncell, w, wx, wy);
 }
-
 
 template <int DIM, int STAGE, bool CG>
 __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
@@ -439,45 +473,25 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   const long nfx = (long)a.ny * (a.nx + 1), nfy = (long)(a.ny + 1) * a.nx;
   const long fxl = (long)j * (a.nx + 1) + i, fyb = (long)j * a.nx + i, fyt = fyb + a.nx;
   const long L = N * ncell;
-  double* accW = a.acc;
-  double* accX = a.acc + L;
-  double* accY = a.acc + 2 * L;
   const double* x64 = reinterpret_cast<const double*>(a.fx);
   const double* y64 = reinterpret_cast<const double*>(a.fy);
+  const float* x32 = reinterpret_cast<const float*>(x64 + 2L * N * nfx);
+  const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 2L * N * nfy) : nullptr;
   const double idx = a.idx, idy = a.idy;
+  const float idxf = (float)idx, idyf = (float)idy;
+  float* M = a.M;
   if (STAGE == 1) {
-    const float* x32 = reinterpret_cast<const float*>(x64 + 1L * N * nfx);
-    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 1L * N * nfy) : nullptr;
-    const long cl = (long)j * a.nx + map_index(i - 1, a.nx, a.bcx);
-    const long cb = DIM == 2 ? (long)map_index(j - 1, a.ny, a.bcy) * a.nx + i : 0;
-    const float idxf = (float)idx, idyf = (float)idy;
-    float* M = a.M;
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      const double W = ldd<CG>(a.W + v * ncell + c);
-      const double* Psi = x64 + (long)v * nfx;
-      const float dOj = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
-      const float dLj = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
-      // W - W* (flux part), single precision: (A_{i+1/2} + D_{i-1/2}) / dx
+      const float* Ox = x32 + (0L * N + v) * nfx;
       float inc = (ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1) + ldf<CG>(x32 + (3L * N + v) * nfx + fxl)) * idxf;
-      const double dW = W - ldd<CG>(a.W + v * ncell + cl);
-      double wa = W - (ldd<CG>(Psi + fxl + 1) - ldd<CG>(Psi + fxl)) * idx;
-      accX[v * ncell + c] = fma(dW, idx, (double)(dLj * idxf));
-      float wxs = ((float)dW + dOj) * idxf;
+      const float wxs = ((float)ldd<CG>(x64 + (long)(N + v) * nfx + fxl) + (ldf<CG>(Ox + fxl + 1) - ldf<CG>(Ox + fxl))) * idxf;
       float wys = 0.f;
       if (DIM == 2) {
-        const double* PsiY = y64 + (long)v * nfy;
-        const float dOy = ldf<CG>(y32 + (0L * N + v) * nfy + fyt) - ldf<CG>(y32 + (0L * N + v) * nfy + fyb);
-        const float dLy = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
+        const float* Oy = y32 + (0L * N + v) * nfy;
         inc += (ldf<CG>(y32 + (2L * N + v) * nfy + fyt) + ldf<CG>(y32 + (3L * N + v) * nfy + fyb)) * idyf;
-        const double dWy = W - ldd<CG>(a.W + v * ncell + cb);
-        wa -= (ldd<CG>(PsiY + fyt) - ldd<CG>(PsiY + fyb)) * idy;
-        accY[v * ncell + c] = fma(dWy, idy, (double)(dLy * idyf));
-        wys = ((float)dWy + dOy) * idyf;
+        wys = ((float)ldd<CG>(y64 + (long)(N + v) * nfy + fyb) + (ldf<CG>(Oy + fyt) - ldf<CG>(Oy + fyb))) * idyf;
       }
-      accW[v * ncell + c] = wa;
-      // W* only as the FP32 mirror read by the stage-2 sweep: this cell's hi/lo mirror of W
-      // plus the single-precision increment, added exactly (two-sum) and renormalised.
       const float d = -inc;
       const float h0 = M[v * ncell + c];
       float lo = M[L + v * ncell + c];
@@ -491,27 +505,30 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       if (DIM == 2) M[3 * L + v * ncell + c] = wys;
     }
   } else {
-    const float* x32 = reinterpret_cast<const float*>(x64 + 1L * N * nfx);
-    const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 1L * N * nfy) : nullptr;
     double w[N], wx[N], wy[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      const double* Th = x64 + (0L * N + v) * nfx;
-      const float Ttj = ldf<CG>(x32 + v * nfx + fxl + 1) - ldf<CG>(x32 + v * nfx + fxl);
-      w[v] = ldd<CG>(accW + v * ncell + c) - (ldd<CG>(Th + fxl + 1) - ldd<CG>(Th + fxl)) * idx;
-      wx[v] = ldd<CG>(accX + v * ncell + c) + (double)Ttj * idx;
+      const double* Xi = x64 + (long)v * nfx;
+      const float* LTx = x32 + (1L * N + v) * nfx;
+      w[v] = ldd<CG>(a.W + v * ncell + c) - (ldd<CG>(Xi + fxl + 1) - ldd<CG>(Xi + fxl)) * idx;
+      wx[v] = fma(ldd<CG>(x64 + (long)(N + v) * nfx + fxl), idx,
+                  (double)((ldf<CG>(LTx + fxl + 1) - ldf<CG>(LTx + fxl)) * idxf));
       wy[v] = 0.0;
       if (DIM == 2) {
-        const double* ThY = y64 + (0L * N + v) * nfy;
-        const float Tty = ldf<CG>(y32 + v * nfy + fyt) - ldf<CG>(y32 + v * nfy + fyb);
-        w[v] -= (ldd<CG>(ThY + fyt) - ldd<CG>(ThY + fyb)) * idy;
-        wy[v] = ldd<CG>(accY + v * ncell + c) + (double)Tty * idy;
+        const double* XiY = y64 + (long)v * nfy;
+        const float* LTy = y32 + (1L * N + v) * nfy;
+        w[v] -= (ldd<CG>(XiY + fyt) - ldd<CG>(XiY + fyb)) * idy;
+        wy[v] = fma(ldd<CG>(y64 + (long)(N + v) * nfy + fyb), idy,
+                    (double)((ldf<CG>(LTy + fyt) - ldf<CG>(LTy + fyb)) * idyf));
       }
-      a.Ws[v * ncell + c] = w[v];
-      a.Ws[L + v * ncell + c] = wx[v];
-      if (DIM == 2) a.Ws[2 * L + v * ncell + c] = wy[v];
     }
-    write_mirror<DIM>(a.M, a.fref, c, ncell, w, wx, wy, a.gamma);
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      a.W[v * ncell + c] = w[v];
+      a.W[L + v * ncell + c] = wx[v];
+      if (DIM == 2) a.W[2 * L + v * ncell + c] = wy[v];
+    }
+    write_mirror<DIM>(M, c, ncell, w, wx, wy);
   }
 }
 
