@@ -33,22 +33,25 @@ import numpy as np  # noqa: E402
 METRIC = "cell-updates/s (2D 8th-order GKS, FP32-bulk vs FP64, isentropic vortex)"
 UNIT = "cell-updates/s"
 CFL = 0.3
-# Algorithmic figures per unit of the kernels that can dominate a step (2D, 8th order, linear
-# Euler), stated with their derivation in the design doc:
-#  - FP64 sweep: FP64 flops per face (FMA = 2), from ncu's executed-instruction counters
-#    (768.6 DFMA + 243.0 DMUL + 130.0 DADD per face; profiles/faces_2d_vortex_fp64.md).
-#  - FP32-bulk sweep: FP32 flops per face, from the same counters (profiles/faces_2d_vortex_fp32bulk.md).
-#  - FP32-bulk updates: bytes per cell read and written once (W, own mirror, one x- and one
-#    y-face's flux parts; accumulators, mirror, reference fluxes) and FP64 flops per cell
-#    counted from the source.
-FLOPS_PER_FACE = {("fp64", 8): 1910.2,
-                  ("fp32", 8): 2222.5}
-UPDATE_MODEL = {"update_stage1": {"bytes_per_cell": 416.0, "f64_flops_per_cell": 68.0},
-                "update_stage2": {"bytes_per_cell": 416.0, "f64_flops_per_cell": 64.0}}
-# DRAM bytes (read + write) per cell of one launch, from an ncu capture of the 1024^2 case
-# scaled by the cell count (streaming kernels: traffic grows in proportion); None where no
-# capture of the current kernel exists.
-TRAFFIC_PER_CELL = {}
+# Per-unit figures of the kernels of a step (2D, 8th order, linear Euler), with their derivation
+# in DESIGN.md.  unit: "face" (sweeps) or "cell" (updates).  f32 / f64: floating-point operations
+# per unit (FMA = 2) from ncu's executed-instruction counters; bytes: algorithmic bytes per unit
+# (each datum read or written once); traffic: DRAM bytes (read + write) per unit from one ncu
+# capture of the 1024^2 case, scaled to a launch by the units processed (the kernels stream,
+# so traffic grows in proportion; at 1024^2 part of the data stays in L2, so it reads low).
+# Sources: profiles/faces_2d_vortex_fp64.md, profiles/faces_2d_vortex_fp32bulk.md.
+KERNEL_MODEL = {
+    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1910.2},
+    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1910.2},
+    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1910.2},
+    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1910.2},
+    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2272.1, "f64": 35.0, "traffic": 158.3},
+    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2164.8, "f64": 35.0, "traffic": 162.7},
+    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0, "traffic": 234.2},
+    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 2116.1, "f64": 4.0, "traffic": 108.2},
+    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 2033.5, "f64": 4.0, "traffic": 110.3},
+    ("fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0, "traffic": 307.1},
+}
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -64,43 +67,40 @@ def hbm_peak():
 
 
 def roofline(form, name, ms, nx, ny, order, peak64, peak32):
-    """Roofline of one launch of kernel `name` taking `ms` milliseconds."""
-    ncell = nx * ny
-    src32 = "FP32 FMA-chain probe measured in this run"
-    src64 = "FP64 FMA-chain probe measured in this run"
-    if name.startswith("update"):
-        m = UPDATE_MODEL.get(name) if form == "fp32" else None
-        if m is None:
-            return {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
-                    "traffic": None, "kernel": name}
-        gbs = m["bytes_per_cell"] * ncell / (ms * 1e-3) / 1e9
+    """Roofline of one launch of kernel `name` taking `ms` milliseconds: the fraction of the
+    FP32 and FP64 peaks (probes measured in this run) and of the HBM bandwidth, the largest
+    named as the bound, the others listed beside it."""
+    m = KERNEL_MODEL.get((form, name)) if order == 8 else None
+    if m is None:
+        return {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": name}
+    if m["unit"] == "face":
+        units = (nx + 1) * ny if name.startswith("x") else nx * (ny + 1)
+    else:
+        units = nx * ny
+    sec = ms * 1e-3
+    cands = []
+    if m.get("f32"):
+        a = m["f32"] * units / sec
+        cands.append({"bound": "alu", "achieved": a / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
+                      "frac": a / peak32, "peak_source": "FP32 FMA-chain probe measured in this run",
+                      "pipe": "fp32", "flops_per_" + m["unit"]: m["f32"]})
+    if m.get("f64"):
+        a = m["f64"] * units / sec
+        cands.append({"bound": "alu", "achieved": a / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                      "frac": a / peak64, "peak_source": "FP64 FMA-chain probe measured in this run",
+                      "pipe": "fp64", "flops_per_" + m["unit"]: m["f64"]})
+    if m.get("bytes"):
         hpeak, hsrc = hbm_peak()
-        tf = m["f64_flops_per_cell"] * ncell / (ms * 1e-3) / 1e12
-        tr = TRAFFIC_PER_CELL.get((form, name))
-        hbm = {"bound": "hbm", "achieved": gbs, "peak": hpeak, "unit": "GB/s", "frac": gbs / hpeak,
-               "traffic": None if tr is None else tr * ncell, "kernel": name, "peak_source": hsrc,
-               "algorithmic_bytes_per_cell": m["bytes_per_cell"]}
-        alu = {"bound": "alu", "achieved": tf, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-               "frac": tf * 1e12 / peak64, "kernel": name, "peak_source": src64,
-               "f64_flops_per_cell": m["f64_flops_per_cell"]}
-        main, other = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
-        main = dict(main)
-        if main["bound"] == "alu":
-            main["traffic"] = hbm["traffic"]
-        main["other_bound"] = {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
-        return main
-    nfaces = (nx + 1) * ny if name.startswith("x") else nx * (ny + 1)
-    fpf = FLOPS_PER_FACE.get((form, order))
-    peak = peak64 if form == "fp64" else peak32
-    roof = {"bound": "alu", "achieved": None, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": None,
-            "traffic": None, "kernel": name, "peak_source": src64 if form == "fp64" else src32}
-    if fpf is not None:
-        achieved = fpf * nfaces / (ms * 1e-3)
-        roof.update(achieved=achieved / 1e12, frac=achieved / peak)
-    tr = TRAFFIC_PER_CELL.get((form, name))
-    if tr is not None:
-        roof["traffic"] = tr * ncell
-    return roof
+        a = m["bytes"] * units / sec / 1e9
+        cands.append({"bound": "hbm", "achieved": a, "peak": hpeak, "unit": "GB/s", "frac": a / hpeak,
+                      "peak_source": hsrc, "bytes_per_" + m["unit"]: m["bytes"]})
+    cands.sort(key=lambda c: -c["frac"])
+    main = dict(cands[0])
+    main["kernel"] = name
+    main["traffic"] = m["traffic"] * units if m.get("traffic") else None
+    main["other_bounds"] = [{k: c[k] for k in ("bound", "achieved", "peak", "unit", "frac")} for c in cands[1:]]
+    return main
 
 
 def parse():
