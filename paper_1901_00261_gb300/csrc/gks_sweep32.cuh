@@ -294,7 +294,9 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
       for (int v = 0; v < N; ++v) dr[v] = in[v][2];
       normal_recon<float, 2, ORDER, WENO>(in, a.dnf, a.gammaf, a.epsf, rec, ref);
       // F_Euler(W_right) - F_Euler(W_ref) of the face's two cells, in the face's frame
-      if (a.stage == 1) euler_flux_delta<float, 2>(ref, dr, a.gammaf, dfc);
+      // only the tile's own face rows (not the tangential halo) use it
+      const bool own = DIR == 0 ? (sb >= 2 && sb < T::TB + 2) : (sa >= 2 && sa < TA32 + 2);
+      if (a.stage == 1 && own) euler_flux_delta<float, 2>(ref, dr, a.gammaf, dfc);
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q)
@@ -348,7 +350,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   const float it = a.itanf;
   float F[N] = {0}, Ft[N] = {0}, dW0[N] = {0}, Wt[N] = {0}, Wtt[N] = {0};
   bool ok = true;
-#pragma unroll 1
+#pragma unroll
   for (int g = 0; g < 3; ++g) {
     PointIn<float, 2> pin;
     float d0[N];
