@@ -12,6 +12,17 @@
 
 namespace gks {
 
+// a / b in the arithmetic type R: the IEEE division for double; for float the fast
+// reciprocal-based division (__fdividef, 2 ulp for 2^-126 < |b| < 2^126), inside the error of
+// the single-precision form, whose inputs already carry single-precision rounding.
+template <typename R> __device__ __forceinline__ R fdiv(R a, R b);
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+// sqrt(x), x > 0, likewise: IEEE for double, x * rsqrtf(x) (a few ulp) for float.
+template <typename R> __device__ __forceinline__ R fsqrt(R x);
+template <> __device__ __forceinline__ double fsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float fsqrt<float>(float x) { return x * rsqrtf(x); }
+
 // ---------------------------------------------------------------------------
 // Compact linear reconstruction (Sec. 3.1): interface value, first and second
 // derivative at x_{i+1/2} from W_{i-1..i+2} and s_k = dx W'_k (printed coefficients of
@@ -92,14 +103,14 @@ __device__ __forceinline__ void weno_left(R Wm, R W0, R W1, R W2, R sm, R s0, R 
   }
   // WENO-Z weights, Eqs. (WENO-Z-w) and (tau)
   R Z = fabs(R(3) * (c0.b - c4.b) + (c4.b - c3.b));
-  R a0 = d0 * (R(1) + Z / (c0.b + eps));
-  R a1 = d1 * (R(1) + Z / (b1 + eps));
-  R a2 = d2 * (R(1) + Z / (c2.b + eps));
-  R a3 = d3 * (R(1) + Z / (c3.b + eps));
-  R a4 = d4 * (R(1) + Z / (c4.b + eps));
-  R a5 = d5 * (R(1) + Z / (c5.b + eps));
-  R a6 = d6 * (R(1) + Z / (c6.b + eps));
-  R inv = R(1) / (a0 + a1 + a2 + a3 + a4 + a5 + a6);
+  R a0 = d0 * (R(1) + fdiv<R>(Z, c0.b + eps));
+  R a1 = d1 * (R(1) + fdiv<R>(Z, b1 + eps));
+  R a2 = d2 * (R(1) + fdiv<R>(Z, c2.b + eps));
+  R a3 = d3 * (R(1) + fdiv<R>(Z, c3.b + eps));
+  R a4 = d4 * (R(1) + fdiv<R>(Z, c4.b + eps));
+  R a5 = d5 * (R(1) + fdiv<R>(Z, c5.b + eps));
+  R a6 = d6 * (R(1) + fdiv<R>(Z, c6.b + eps));
+  R inv = fdiv<R>(R(1), a0 + a1 + a2 + a3 + a4 + a5 + a6);
   // w_1 and w_3 share point value and slope
   val = (a0 * c0.v + (a1 + a3) * c3.v + a2 * c2.v + a4 * c4.v + a5 * c5.v + a6 * c6.v) * inv;
   dh = (a0 * c0.d + (a1 + a3) * c3.d + a2 * c2.d + a4 * c4.d + a5 * c5.d + a6 * c6.d) * inv;
@@ -118,16 +129,16 @@ struct Eig {
 template <typename R, int DIM>
 __device__ __forceinline__ Eig<R, DIM> eig_at(const R* W, R gamma) {
   Eig<R, DIM> e;
-  R irho = R(1) / W[0];
+  R irho = fdiv<R>(R(1), W[0]);
   e.U = W[1] * irho;
   e.V = DIM == 2 ? W[2] * irho : R(0);
   R q2 = e.U * e.U + e.V * e.V;
   R p = (gamma - R(1)) * (W[DIM + 1] - R(0.5) * W[0] * q2);
   R c2 = gamma * p * irho;
-  e.c = sqrt(c2);
-  e.ic = R(1) / e.c;
+  e.c = fsqrt<R>(c2);
+  e.ic = fdiv<R>(R(1), e.c);
   e.H = (W[DIM + 1] + p) * irho;
-  e.b1 = (gamma - R(1)) / c2;
+  e.b1 = fdiv<R>(gamma - R(1), c2);
   e.b2 = R(0.5) * q2 * e.b1;
   return e;
 }
@@ -176,18 +187,18 @@ struct Maxw {
 template <typename R, int DIM>
 __device__ __forceinline__ bool maxw_prim(const R* W, R gamma, R K, Maxw<R, DIM>& g) {
   g.rho = W[0];
-  const R irho = R(1) / g.rho;
+  const R irho = fdiv<R>(R(1), g.rho);
   g.U = W[1] * irho;
   g.V = DIM == 2 ? W[2] * irho : R(0);
   g.p = (gamma - R(1)) * (W[DIM + 1] - R(0.5) * g.rho * (g.U * g.U + g.V * g.V));
-  g.lam = R(0.5) * g.rho / g.p;
+  g.lam = fdiv<R>(R(0.5) * g.rho, g.p);
   R h = g.p * irho;      // variance 1/(2 lam) = p / rho
   g.x1 = K * h;
   g.x2 = K * (K + R(2)) * h * h;
   g.irho = irho;
   g.Q = g.U * g.U + g.V * g.V + (K + R(DIM)) * h;
   g.lam2 = R(2) * g.lam;
-  g.cK = g.lam2 * g.lam2 / (K + R(DIM));
+  g.cK = fdiv<R>(g.lam2 * g.lam2, K + R(DIM));
   if (DIM == 2) {
     g.n[0] = R(1); g.n[1] = g.V;
 #pragma unroll
@@ -209,10 +220,10 @@ __device__ __forceinline__ void maxw_full(Maxw<R, DIM>& g) {
 template <typename R, int DIM>
 __device__ __forceinline__ void maxw_half(Maxw<R, DIM>& g, int sign) {
   R h = g.p * g.irho;
-  R sl = sqrt(g.lam);
+  R sl = fsqrt<R>(g.lam);
   R s = sign > 0 ? R(1) : R(-1);
   g.m[0] = R(0.5) * erfc(-s * sl * g.U);
-  g.m[1] = g.U * g.m[0] + s * R(0.5) * exp(-g.lam * g.U * g.U) / (sl * R(1.7724538509055160273));
+  g.m[1] = g.U * g.m[0] + fdiv<R>(s * R(0.5) * exp(-g.lam * g.U * g.U), sl * R(1.7724538509055160273));
 #pragma unroll
   for (int k = 1; k < 6; ++k) g.m[k + 1] = g.U * g.m[k] + R(k) * h * g.m[k - 1];
 }
@@ -394,7 +405,7 @@ struct PointOut {
 // only the parts odd in a and even in b survive the average.
 template <typename R, int DIM>
 __device__ __forceinline__ R heat_lin(const Maxw<R, DIM>& g, const R* cu, const R* cv, const R* c0) {
-  R h = R(0.5) / g.lam;
+  R h = fdiv<R>(R(0.5), g.lam);
   R U = g.U, V = DIM == 2 ? g.V : R(0);
   R bb2 = DIM == 2 ? h : R(0);                 // <b^2>
   R bb4 = DIM == 2 ? R(3) * h * h : R(0);      // <b^4>
@@ -428,7 +439,7 @@ template <typename R, int DIM>
 __device__ __forceinline__ Flow<R, DIM> flow_of(const R* W, R gamma) {
   Flow<R, DIM> f;
   f.rho = W[0];
-  f.irho = R(1) / f.rho;
+  f.irho = fdiv<R>(R(1), f.rho);
   f.U = W[1] * f.irho;
   f.V = DIM == 2 ? W[2] * f.irho : R(0);
   f.q2h = R(0.5) * (f.U * f.U + f.V * f.V);
@@ -493,8 +504,8 @@ __device__ __forceinline__ void euler_flux_delta(const R* r, const R* d, R gamma
   const int N = DIM + 2;
   R rho = r[0], m = r[1], n = DIM == 2 ? r[2] : R(0), E = r[N - 1];
   R drho = d[0], dm = d[1], dn = DIM == 2 ? d[2] : R(0), dE = d[N - 1];
-  R irho = R(1) / rho;
-  R q = irho / (rho + drho);                             // 1 / (rho (rho + drho))
+  R irho = fdiv<R>(R(1), rho);
+  R q = fdiv<R>(irho, rho + drho);                             // 1 / (rho (rho + drho))
   R U = m * irho, V = n * irho;
   R dmm = (rho * dm * (R(2) * m + dm) - m * m * drho) * q;    // d(m^2/rho)
   R dnn = (rho * dn * (R(2) * n + dn) - n * n * drho) * q;    // d(n^2/rho)
@@ -575,7 +586,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       // Chapman-Enskog bracket with the physical collision time mu/p (reading R1):
       // -tau rho<u psi (a1 u + a2 v + A)> and -tau rho<u psi (a_xt u + a_yt v + a_tt)>,
       // where rho<u psi A> = A_n W_t = F_t and rho<u psi a_tt> = A_n W_tt.
-      R tau = R(P.mu) / g0.p;
+      R tau = fdiv<R>(R(P.mu), g0.p);
       R A[N], axt[N], ayt[N], att[N], Fvt[N];
       maxw_solve<R, DIM>(g0, Wt, A);
       maxw_solve<R, DIM>(g0, Wxt, axt);
