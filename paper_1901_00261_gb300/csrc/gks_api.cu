@@ -77,7 +77,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     fa.dnf = (float)c->dx; fa.gammaf = (float)c->P.gamma; fa.epsf = (float)c->P.weno_eps;
     const bool visc = c->P.mu > 0.0;
     gks::UpdateArgs32 ua;
-    ua.fx = reinterpret_cast<const float*>(c->fx); ua.fy = reinterpret_cast<const float*>(c->fy);
+    ua.fx = reinterpret_cast<float*>(c->fx); ua.fy = reinterpret_cast<float*>(c->fy);
     ua.W = c->state; ua.M = c->mirror;
     ua.nx = c->nx; ua.ny = c->ny; ua.bcx = c->o.bc_x; ua.bcy = c->o.bc_y;
     ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy;

@@ -444,7 +444,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
       }
     }
     gks::UpdateArgs32& u = P.up;
-    u.W = state; u.fx = reinterpret_cast<const float*>(fx); u.fy = reinterpret_cast<const float*>(fy);
+    u.W = state; u.fx = reinterpret_cast<float*>(fx); u.fy = reinterpret_cast<float*>(fy);
     u.M = mir;
     u.nx = q.nx; u.ny = q.ny; u.bcx = q.bc_x; u.bcy = q.bc_y;
     u.idx = 1.0 / dx; u.idy = 1.0 / dy;

@@ -73,8 +73,8 @@ struct FaceArgs32 {
 // FP32-bulk cell update: FP64 accumulation; writes the next mirror.
 struct UpdateArgs32 {
   double* W;           // FP64 state [W | Wx (| Wy)][nv][ny][nx]: W^n read and W^{n+1} written (stage 2)
-  const float* fx;     // x-face buffer (FP64 planes, then FP32 planes; see write_face32)
-  const float* fy;     // y-face buffer (2D)
+  float* fx;           // x-face buffer (FP64 planes, then FP32 planes; see write_face32)
+  float* fy;           // y-face buffer (2D)
   float* M;            // FP32 mirror: W^n / W* / W^{n+1} (hi, lo, Wx, Wy planes)
   int nx, ny, bcx, bcy;
   double idx, idy;

@@ -114,7 +114,8 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
 //   FP64 dW  = W_right - W_left of the face's two cells    (stage 1)
 //   FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt     (stage 1)
 //   FP32 dLT = W0 - W_ref + dt W_t + dt^2/6 W_tt          (stage 1; stage 2 adds dt^2/3 W_tt*)
-//   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1)
+//   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1; the stage-1 update then
+//        replaces D by the single-precision cell difference float(dW))
 // F_ref = F_Euler(W_left) in FP64 (W_ref = W_left is the face's reference state), dF and F_t the
 // single-precision flux delta and derivative, dFc = F_Euler(W_right) - F_Euler(W_left) in the
 // single-precision delta form.  Xi is one FP64 value per face, so its differences across a
@@ -429,7 +430,9 @@ __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_
 //     of W^n plus the single-precision increment -(A_{i+1/2} + D_{i-1/2})/dx - (..)/dy, added
 //     exactly (two-sum) and renormalised; the W* slopes (dW + dOmega_{i+1/2} - dOmega_{i-1/2})/dx
 //     as floats.
-//   Stage 2: W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
+//   Stage 2 (float mirror of the slopes: (float(dW) + dLT_{i+1/2} - dLT_{i-1/2})/dx, single
+//     precision, float(dW) left in the D plane by stage 1):
+//     W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
 //     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
 //     place (each cell reads only its own state), and the mirror of W^{n+1}.
 // ---------------------------------------------------------------------------
@@ -477,29 +480,50 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   const long L = N * ncell;
   const double* x64 = reinterpret_cast<const double*>(a.fx);
   const double* y64 = reinterpret_cast<const double*>(a.fy);
-  const float* x32 = reinterpret_cast<const float*>(x64 + 2L * N * nfx);
-  const float* y32 = DIM == 2 ? reinterpret_cast<const float*>(y64 + 2L * N * nfy) : nullptr;
+  float* x32 = a.fx + 4L * N * nfx;   // after the 2N FP64 planes
+  float* y32 = DIM == 2 ? a.fy + 4L * N * nfy : nullptr;
   const double idx = a.idx, idy = a.idy;
   const float idxf = (float)idx, idyf = (float)idy;
   float* M = a.M;
   if (STAGE == 1) {
+    // all loads first (the D-plane stores below could otherwise alias them and serialise)
+    float h0[N], lo0[N], Ax[N], Dxv[N], Ol[N], Or[N], dWx[N];
+    float Ay[N], Dyv[N], Ob[N], Ot[N], dWy[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      const float* Ox = x32 + (0L * N + v) * nfx;
-      float inc = (ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1) + ldf<CG>(x32 + (3L * N + v) * nfx + fxl)) * idxf;
-      const float wxs = ((float)ldd<CG>(x64 + (long)(N + v) * nfx + fxl) + (ldf<CG>(Ox + fxl + 1) - ldf<CG>(Ox + fxl))) * idxf;
+      h0[v] = M[v * ncell + c];
+      lo0[v] = M[L + v * ncell + c];
+      Ol[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
+      Or[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1);
+      Ax[v] = ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1);
+      Dxv[v] = ldf<CG>(x32 + (3L * N + v) * nfx + fxl);
+      dWx[v] = (float)ldd<CG>(x64 + (long)(N + v) * nfx + fxl);
+      if (DIM == 2) {
+        Ob[v] = ldf<CG>(y32 + (0L * N + v) * nfy + fyb);
+        Ot[v] = ldf<CG>(y32 + (0L * N + v) * nfy + fyt);
+        Ay[v] = ldf<CG>(y32 + (2L * N + v) * nfy + fyt);
+        Dyv[v] = ldf<CG>(y32 + (3L * N + v) * nfy + fyb);
+        dWy[v] = (float)ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      float inc = (Ax[v] + Dxv[v]) * idxf;   // (A_{i+1/2} + D_{i-1/2}) / dx
+      const float wxs = (dWx[v] + (Or[v] - Ol[v])) * idxf;
       float wys = 0.f;
       if (DIM == 2) {
-        const float* Oy = y32 + (0L * N + v) * nfy;
-        inc += (ldf<CG>(y32 + (2L * N + v) * nfy + fyt) + ldf<CG>(y32 + (3L * N + v) * nfy + fyb)) * idyf;
-        wys = ((float)ldd<CG>(y64 + (long)(N + v) * nfy + fyb) + (ldf<CG>(Oy + fyt) - ldf<CG>(Oy + fyb))) * idyf;
+        inc += (Ay[v] + Dyv[v]) * idyf;
+        wys = (dWy[v] + (Ot[v] - Ob[v])) * idyf;
       }
+      // D at this cell's left (bottom) face is read only by this cell: it is replaced by the
+      // FP32 cell difference dW, which the stage-2 update uses for the float mirror of the slopes
+      x32[(3L * N + v) * nfx + fxl] = dWx[v];
+      if (DIM == 2) y32[(3L * N + v) * nfy + fyb] = dWy[v];
+      // W* = W + d as hi/lo: exact two-sum of the cell's hi with d, renormalised
       const float d = -inc;
-      const float h0 = M[v * ncell + c];
-      float lo = M[L + v * ncell + c];
-      const float s1 = h0 + d;
-      const float bb = s1 - h0;
-      lo += (h0 - (s1 - bb)) + (d - bb);
+      const float s1 = h0[v] + d;
+      const float bb = s1 - h0[v];
+      const float lo = lo0[v] + ((h0[v] - (s1 - bb)) + (d - bb));
       const float hi = s1 + lo;
       M[v * ncell + c] = hi;
       M[L + v * ncell + c] = lo - (hi - s1);
@@ -507,30 +531,41 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       if (DIM == 2) M[3 * L + v * ncell + c] = wys;
     }
   } else {
-    double w[N], wx[N], wy[N];
+    // all loads first, then the FP64 accumulation and the stores
+    double W0[N], Xl[N], Xr[N], dWx[N], Yb[N], Yt[N], dWy[N];
+    float dLx[N], fWx[N], dLy[N], fWy[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      const double* Xi = x64 + (long)v * nfx;
-      const float* LTx = x32 + (1L * N + v) * nfx;
-      w[v] = ldd<CG>(a.W + v * ncell + c) - (ldd<CG>(Xi + fxl + 1) - ldd<CG>(Xi + fxl)) * idx;
-      wx[v] = fma(ldd<CG>(x64 + (long)(N + v) * nfx + fxl), idx,
-                  (double)((ldf<CG>(LTx + fxl + 1) - ldf<CG>(LTx + fxl)) * idxf));
-      wy[v] = 0.0;
+      W0[v] = ldd<CG>(a.W + v * ncell + c);
+      Xl[v] = ldd<CG>(x64 + (long)v * nfx + fxl);
+      Xr[v] = ldd<CG>(x64 + (long)v * nfx + fxl + 1);
+      dWx[v] = ldd<CG>(x64 + (long)(N + v) * nfx + fxl);
+      dLx[v] = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
+      fWx[v] = ldf<CG>(x32 + (3L * N + v) * nfx + fxl);
       if (DIM == 2) {
-        const double* XiY = y64 + (long)v * nfy;
-        const float* LTy = y32 + (1L * N + v) * nfy;
-        w[v] -= (ldd<CG>(XiY + fyt) - ldd<CG>(XiY + fyb)) * idy;
-        wy[v] = fma(ldd<CG>(y64 + (long)(N + v) * nfy + fyb), idy,
-                    (double)((ldf<CG>(LTy + fyt) - ldf<CG>(LTy + fyb)) * idyf));
+        Yb[v] = ldd<CG>(y64 + (long)v * nfy + fyb);
+        Yt[v] = ldd<CG>(y64 + (long)v * nfy + fyt);
+        dWy[v] = ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
+        dLy[v] = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
+        fWy[v] = ldf<CG>(y32 + (3L * N + v) * nfy + fyb);
       }
     }
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      a.W[v * ncell + c] = w[v];
-      a.W[L + v * ncell + c] = wx[v];
-      if (DIM == 2) a.W[2 * L + v * ncell + c] = wy[v];
+      double w = W0[v] - (Xr[v] - Xl[v]) * idx;
+      a.W[L + v * ncell + c] = fma(dWx[v], idx, (double)(dLx[v] * idxf));
+      M[2 * L + v * ncell + c] = (fWx[v] + dLx[v]) * idxf;   // (dW + dLT_{i+1/2} - dLT_{i-1/2}) / dx
+      if (DIM == 2) {
+        w -= (Yt[v] - Yb[v]) * idy;
+        a.W[2 * L + v * ncell + c] = fma(dWy[v], idy, (double)(dLy[v] * idyf));
+        M[3 * L + v * ncell + c] = (fWy[v] + dLy[v]) * idyf;
+      }
+      a.W[v * ncell + c] = w;
+      float hi, lo;
+      split_hilo(w, hi, lo);
+      M[v * ncell + c] = hi;
+      M[L + v * ncell + c] = lo;
     }
-    write_mirror<DIM>(M, c, ncell, w, wx, wy);
   }
 }
 
