@@ -31,26 +31,33 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "cell-updates/s (2D 8th-order GKS, FP32-bulk vs FP64, isentropic vortex)"
+METRIC_SHEAR = "cell-updates/s (2D 8th-order GKS, FP32-bulk vs FP64, Navier-Stokes WENO-Z shear layer)"
+
+
+def metric_of(args):
+    return METRIC_SHEAR if args.workload == "shear" else METRIC
 UNIT = "cell-updates/s"
 CFL = 0.3
 # Per-unit figures of the kernels of a step (2D, 8th order, linear Euler), with their derivation
 # in DESIGN.md.  unit: "face" (sweeps) or "cell" (updates).  f32 / f64: floating-point operations
 # per unit (FMA = 2) from ncu's executed-instruction counters; bytes: algorithmic bytes per unit
-# (each datum read or written once); traffic: DRAM bytes (read + write) per unit from one ncu
-# capture of the 1024^2 case, scaled to a launch by the units processed (the kernels stream,
-# so traffic grows in proportion; at 1024^2 part of the data stays in L2, so it reads low).
+# (each datum read or written once), given for the updates, whose limit is memory or the FP64
+# pipe (the sweeps are compute-side: issue-bound, DRAM below 20 %); traffic: DRAM bytes (read +
+# write) per unit from one ncu capture of the 1024^2 case, scaled to a launch by the units
+# processed (the kernels stream, so traffic grows in proportion; at 1024^2 part of the data
+# stays in L2, so it reads low).
 # Sources: profiles/faces_2d_vortex_fp64.md, profiles/faces_2d_vortex_fp32bulk.md.
 KERNEL_MODEL = {
     ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1910.2},
     ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1910.2},
     ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1910.2},
     ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1910.2},
-    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2272.1, "f64": 35.0, "traffic": 158.3},
-    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2164.8, "f64": 35.0, "traffic": 162.7},
-    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0, "traffic": 234.2},
-    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 2116.1, "f64": 4.0, "traffic": 108.2},
-    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 2033.5, "f64": 4.0, "traffic": 110.3},
-    ("fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0, "traffic": 307.1},
+    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2164.1, "f64": 35.0, "traffic": 157.6},
+    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2073.5, "f64": 35.0, "traffic": 161.5},
+    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 250.1},
+    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 2052.1, "f64": 4.0, "traffic": 108.2},
+    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1961.5, "f64": 4.0, "traffic": 109.3},
+    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 345.0},
 }
 HBM_FALLBACK_GBS = 6800.0
 
@@ -109,15 +116,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--n", type=int, default=None,
+                    help="grid side (default 2048 for vortex, 4096 for shear)")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-acc", action="store_true", help="skip the L1 error against the exact solution")
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "batch"],
-                    help="vortex: the 2D benchmark workload; batch: the mixed batch of 512 "
-                         "problems (persistent launch, FP32-bulk)")
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "shear", "batch"],
+                    help="vortex: the 2D benchmark workload (8th-order linear isentropic vortex); "
+                         "shear: the Navier-Stokes double shear layer (8th-order WENO-Z, 4096^2); "
+                         "batch: the mixed batch of 512 problems (persistent launch, FP32-bulk)")
     ap.add_argument("--batch-count", type=int, default=512)
     return ap.parse_args()
 
@@ -210,7 +219,10 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     from paper_1901_00261_gb300 import inputs
-    st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
+    if args.workload == "shear":
+        st = inputs.shear_layer_2d(args.n, order=args.order)
+    else:
+        st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
     import oracle
     O = oracle.Solver(8, 8)  # builds the library before timing
     del O
@@ -228,7 +240,7 @@ def run_reference(args, ws, rank):
     val = statistics.median([r["value"] for r in per_step])
     cb = dict(per_step[-1])
     cb["value"] = val
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_of(args), "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * st.nx * st.ny / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
@@ -238,6 +250,12 @@ def run_reference(args, ws, rank):
 
 
 def workload_config(args):
+    if args.workload == "shear":
+        return {"workload": f"shear_layer_2d_ns_{args.n}x{args.n}", "cells": args.n * args.n,
+                "order": args.order, "recon": "wenoz", "mu": 1e-4, "Pr": 0.72,
+                "precision": "fp32-bulk (headline) and fp64", "cfl": CFL, "domain": "periodic [0,1]^2",
+                "l2_policy": "inputs exceed L2 (state 12 x 8 B per cell)",
+                "parallelism": f"replicas x{args.gpus}"}
     return {"workload": f"isentropic_vortex_2d_{args.n}x{args.n}", "cells": args.n * args.n,
             "order": args.order, "recon": "linear", "precision": "fp32-bulk (headline) and fp64", "cfl": CFL,
             "domain": "periodic [0,10]^2", "l2_policy": "inputs exceed L2 (state 12 x 8 B per cell)",
@@ -315,6 +333,8 @@ def run_batch(args, ws, rank, local):
 
 def main():
     args = parse()
+    if args.n is None:
+        args.n = 4096 if args.workload == "shear" else 2048
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -332,7 +352,10 @@ def main():
         torch.cuda.set_device(0)
     from paper_1901_00261_gb300 import gks, inputs
 
-    st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
+    if args.workload == "shear":
+        st = inputs.shear_layer_2d(args.n, order=args.order)
+    else:
+        st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
     stream = torch.cuda.current_stream()
     ncell = st.nx * st.ny
     slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
@@ -379,8 +402,9 @@ def main():
         if not args.no_acc and rank == 0:
             T = dt * (args.warmup + args.steps)
             W, _, _ = G.get_state()
-            ex = inputs.vortex_exact_avg(args.n, T)
-            r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
+            if args.workload == "vortex":
+                ex = inputs.vortex_exact_avg(args.n, T)
+                r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
             r["t_end"] = T
             results.setdefault("_W", {})[form] = W[0]
         results[form] = r
@@ -418,7 +442,7 @@ def main():
 
     if rank == 0:
         h = results[head]
-        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        line = {"metric": metric_of(args), "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-bulk (f64 time coefficients and accumulation)" if head == "fp32" else "f64",

@@ -333,6 +333,22 @@ __device__ __forceinline__ void gcol0(const Gm<R, DIM>& G, R s, R* out, bool acc
 // ---------------------------------------------------------------------------
 struct TimeCoef { double a0, a1, b0, b1; };
 
+// Taylor coefficients of 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x) for
+// phi(y) = 1 - e^{-y}(1 + y) = sum_{k>=2} (-1)^k (k-1) y^k / k!, k = 2..21 (the first omitted
+// term is below 1e-13 of the sum for x < 1), formed at compile time.
+struct PhiSeries { double a[22], b[22]; };
+__host__ __device__ constexpr PhiSeries make_phi_series() {
+  PhiSeries c{};
+  double fact = 1.0, p2 = 1.0;
+  for (int k = 0; k < 22; ++k) {
+    if (k > 0) { fact *= k; p2 *= 2.0; }
+    const double sg = (k & 1) ? -1.0 : 1.0;
+    c.a[k] = k >= 2 ? sg * (k - 1) * (4.0 - p2) / fact : 0.0;
+    c.b[k] = k >= 2 ? sg * (k - 1) * (p2 - 2.0) / fact : 0.0;
+  }
+  return c;
+}
+
 __device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
   TimeCoef T;
   double h = 0.5 * dt, x = h / tau;
@@ -343,19 +359,17 @@ __device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
   T.b0 = -4.0 * tau * S * S * idt * idt;
   double pa, pb;   // 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x), phi(y) = 1 - e^{-y}(1+y)
   if (x < 1.0) {
-    // phi(y) = sum_{k>=2} (-1)^k (k-1) y^k / k!
-    double term = x * x * 0.5;   // x^k / k! at k = 2
-    double p2 = 4.0;             // 2^k
-    pa = 0.0; pb = 0.0;
+    // the series, by Horner's rule in x (x^2 factored out)
+    constexpr PhiSeries C = make_phi_series();
+    double qa = C.a[21], qb = C.b[21];
 #pragma unroll
-    for (int k = 2; k < 22; ++k) {
-      double sg = (k & 1) ? -1.0 : 1.0;
-      double ck = sg * (double)(k - 1) * term;
-      pa += ck * (4.0 - p2);
-      pb += ck * (p2 - 2.0);
-      term *= x / (double)(k + 1);
-      p2 *= 2.0;
+    for (int k = 20; k >= 2; --k) {
+      qa = fma(qa, x, C.a[k]);
+      qb = fma(qb, x, C.b[k]);
     }
+    const double x2 = x * x;
+    pa = qa * x2;
+    pb = qb * x2;
   } else {
     double e = 1.0 - S;   // e^{-x}
     double e2 = e * e;
