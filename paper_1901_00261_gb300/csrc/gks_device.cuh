@@ -349,14 +349,16 @@ __host__ __device__ constexpr PhiSeries make_phi_series() {
   return c;
 }
 
-__device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
+// Arguments in terms of theta = tau/dt and x = (dt/2)/tau = 1/(2 theta) (both formed by the
+// caller in its arithmetic type; the cancellation is inside the formulas below, which run in
+// FP64): a0 = theta S (2 + S), b0 = -4 theta S^2 / dt, a1 = theta^2 dt pa, b1 = 4 theta^2 pb.
+__device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt) {
   TimeCoef T;
-  double h = 0.5 * dt, x = h / tau;
   // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
   double S = x > 40.0 ? 1.0 : -expm1(-x);
   double idt = 1.0 / dt;
-  T.a0 = tau * S * (2.0 + S) * idt;
-  T.b0 = -4.0 * tau * S * S * idt * idt;
+  T.a0 = theta * S * (2.0 + S);
+  T.b0 = -4.0 * theta * S * S * idt;
   double pa, pb;   // 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x), phi(y) = 1 - e^{-y}(1+y)
   if (x < 1.0) {
     // the series, by Horner's rule in x (x^2 factored out)
@@ -376,9 +378,9 @@ __device__ __forceinline__ TimeCoef time_coefs(double dt, double tau) {
     pa = 3.0 - 4.0 * e * (1.0 + x) + e2 * (1.0 + 2.0 * x);
     pb = -1.0 + 2.0 * e * (1.0 + x) - e2 * (1.0 + 2.0 * x);
   }
-  double t2 = tau * tau;
-  T.a1 = t2 * pa * idt;
-  T.b1 = 4.0 * t2 * pb * idt * idt;
+  const double t2 = theta * theta;
+  T.a1 = t2 * pa * dt;
+  T.b1 = 4.0 * t2 * pb;
   return T;
 }
 
@@ -634,10 +636,10 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       // Non-equilibrium branch: -e^{-t/tau} g0 [1 - (a1 u + a2 v) t] + H g_l [...] + (1-H) g_r [...]
       // time-integrated over [0, dt/2] and [0, dt] and fitted linearly (FP64 coefficients).
       // rho0 <u psi> = F_Euler(W0).
-      double p0 = (double)g0.p;
-      double jump = P.C_tau * fabs(((double)pl - (double)pr) / ((double)pl + (double)pr)) * dt;
-      double taun = (P.mu > 0.0 ? P.mu / p0 : P.eps_tau * dt) + jump;
-      TimeCoef T = time_coefs(dt, taun);
+      // theta = tau_n / dt (Sec. 4: mu/p, or eps dt, plus C |pl - pr| / (pl + pr) dt)
+      const R theta = (P.mu > 0.0 ? fdiv<R>(R(P.mu), g0.p * R(dt)) : R(P.eps_tau)) +
+                      R(P.C_tau) * fabs(fdiv<R>(pl - pr, pl + pr));
+      const TimeCoef T = time_coefs((double)theta, (double)fdiv<R>(R(0.5), theta), dt);
       R c0[N], c1[N];
 #pragma unroll
       for (int k = 0; k < N; ++k) c0[k] = -F[k];
@@ -667,10 +669,13 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
           gmul<R, DIM, true>(H11, ak2, -gk.rho, c1);
         }
       }
+      // the coefficients in the arithmetic type (FP64 for the FP64 form; rounded once to float
+      // for the single-precision form, whose inputs c0, c1, F carry single-precision error)
+      const R a0 = R(T.a0), a1 = R(T.a1), b0 = R(T.b0), b1 = R(T.b1);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        F[k] = R((double)F[k] + T.a0 * (double)c0[k] + T.a1 * (double)c1[k]);
-        Ft[k] = R((double)Ft[k] + T.b0 * (double)c0[k] + T.b1 * (double)c1[k]);
+        F[k] = F[k] + a0 * c0[k] + a1 * c1[k];
+        Ft[k] = Ft[k] + b0 * c0[k] + b1 * c1[k];
       }
     }
   }

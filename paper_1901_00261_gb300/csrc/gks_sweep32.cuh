@@ -351,7 +351,8 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   const float it = a.itanf;
   float F[N] = {0}, Ft[N] = {0}, dW0[N] = {0}, Wt[N] = {0}, Wtt[N] = {0};
   bool ok = true;
-#pragma unroll
+  // unrolled for the linear Euler tile; the WENO-Z / viscous tiles are register-bound
+#pragma unroll ((WENO || VISC) ? 1 : 3)
   for (int g = 0; g < 3; ++g) {
     PointIn<float, 2> pin;
     float d0[N];
