@@ -14,6 +14,7 @@ import pytest
 
 from paper_1901_00261_gb300 import gks, inputs
 import acoustic_exact
+import riemann_exact
 
 pytestmark = pytest.mark.gpu
 
@@ -129,6 +130,38 @@ def test_fp32_bulk_acoustic_wave():
         errs[prec] = np.abs(W[0, 0] - acoustic_exact.cell_average_density(N, T)).max() / acoustic_exact.amplitude()
     assert errs[gks.PREC_FP32_BULK] < 1e-3, errs
     assert abs(errs[gks.PREC_FP32_BULK] - errs[gks.PREC_FP64]) < 1e-4, errs
+
+
+def _run_to(st, T, prec):
+    S = gks.Solver.from_state(st, precision=prec)
+    n = math.ceil(T / (0.3 / S.max_wavespeed()))
+    S.steps(T / n, n)
+    W, _, _ = S.get_state()
+    S.close()
+    return W
+
+
+def test_fp32_bulk_shu_osher_against_fine_reference():
+    """Shu-Osher (8th-order WENO-Z, N = 400, t = 1.8): L1 density error against a 12800-cell
+    FP64 run averaged onto the 400 cells.  The FP32-bulk form's error is within 5 % of the FP64
+    form's (the single-precision rounding is far below the discretisation error here)."""
+    T, N, R = 1.8, 400, 32
+    ref = _run_to(inputs.shu_osher_1d(N * R), T, gks.PREC_FP64)[0, 0].reshape(N, R).mean(axis=1)
+    e = {p: np.abs(_run_to(inputs.shu_osher_1d(N), T, p)[0, 0] - ref).mean()
+         for p in (gks.PREC_FP64, gks.PREC_FP32_BULK)}
+    assert e[gks.PREC_FP64] < 0.05, e
+    assert e[gks.PREC_FP32_BULK] <= 1.05 * e[gks.PREC_FP64], e
+
+
+def test_fp32_bulk_sod_against_exact():
+    """Sod tube (8th-order WENO-Z, N = 1000, t = 0.2): L1 density error against the exact
+    Riemann solution's cell averages; the FP32-bulk form within 5 % of the FP64 form."""
+    T, N = 0.2, 1000
+    ex = riemann_exact.cell_average_density(N, 0.0, 1.0, 0.5, T, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    e = {p: np.abs(_run_to(inputs.sod_1d(N), T, p)[0, 0] - ex).mean()
+         for p in (gks.PREC_FP64, gks.PREC_FP32_BULK)}
+    assert e[gks.PREC_FP64] < 2e-3, e
+    assert e[gks.PREC_FP32_BULK] <= 1.05 * e[gks.PREC_FP64], e
 
 
 def test_fp32_bulk_set_state_refreshes_mirror():
