@@ -23,6 +23,13 @@
 //     interface-value MSMD plus the Gauss slope formula of Sec. 2.2 / Eq.
 //     (Gausian-formula).
 //
+// Pins (tests/test_oracle_*.py): every function above is checked against something other
+// than itself -- printed coefficients, polynomial exactness, closed forms, quadrature, the
+// exact Euler/Navier-Stokes fluxes it must reduce to, the paper's accuracy tables, exact
+// Riemann, vortex and linear-acoustics solutions.  Whole runs of the Shu-Osher problem, the
+// shear layer and the random Riemann problems have no exact solution: for those the parity is
+// unpinned beyond conservation and positivity.
+//
 // Readings taken where the paper is silent or garbled (each one is listed with its
 // reason in the project's design notes):
 //   R1  the Chapman-Enskog bracket uses the physical collision time mu/p (0 for the
