@@ -74,21 +74,27 @@ __device__ __forceinline__ void run_item(const BatchProblem& P, int phase, int k
 #pragma unroll 1
       for (int r = 0; r < FPT; ++r) {
         const int f = base + r * (TA32 * TB32) + tid;
+        // the MSMD stage (index 0 / 1) picks the stage-1 / stage-2 instantiation
+#define GKS_SWEEP1D(O, WN, VS) \
+  (stage == 0 ? sweep1d_f32_face_call<O, WN, VS, 1>(a, f) : sweep1d_f32_face_call<O, WN, VS, 2>(a, f))
         if (P.order == 6) {
-          if (P.recon == 0) sweep1d_f32_face_call<6, false, false>(a, f);
-          else if (CLASS == 1 && visc) sweep1d_f32_face_call<6, true, true>(a, f);
-          else sweep1d_f32_face_call<6, true, false>(a, f);
+          if (P.recon == 0) GKS_SWEEP1D(6, false, false);
+          else if (CLASS == 1 && visc) GKS_SWEEP1D(6, true, true);
+          else GKS_SWEEP1D(6, true, false);
         } else {
-          if (P.recon == 0) sweep1d_f32_face_call<8, false, false>(a, f);
-          else if (CLASS == 1 && visc) sweep1d_f32_face_call<8, true, true>(a, f);
-          else sweep1d_f32_face_call<8, true, false>(a, f);
+          if (P.recon == 0) GKS_SWEEP1D(8, false, false);
+          else if (CLASS == 1 && visc) GKS_SWEEP1D(8, true, true);
+          else GKS_SWEEP1D(8, true, false);
         }
       }
+#undef GKS_SWEEP1D
       return;
     }
     const int tbx = kind == 0 ? P.tbx_x : P.tbx_y;
     const int bx = tile % tbx, by = tile / tbx;
-#define GKS_SWEEP2D(O, WN, VS, D) sweep2d_f32_tile_call<O, WN, VS, D, FPT>(a, bx, by, tid, smf)
+#define GKS_SWEEP2D(O, WN, VS, D)                                          \
+  (stage == 0 ? sweep2d_f32_tile_call<O, WN, VS, D, FPT, 1>(a, bx, by, tid, smf) \
+              : sweep2d_f32_tile_call<O, WN, VS, D, FPT, 2>(a, bx, by, tid, smf))
     if (CLASS == 0) {
       if (kind == 0) { if (P.order == 6) GKS_SWEEP2D(6, false, false, 0); else GKS_SWEEP2D(8, false, false, 0); }
       else { if (P.order == 6) GKS_SWEEP2D(6, false, false, 1); else GKS_SWEEP2D(8, false, false, 1); }

@@ -538,7 +538,10 @@ __device__ __forceinline__ void euler_flux_delta(const R* r, const R* d, R gamma
 // the nonlinear functions), d0 the delta of the linear reconstruction value; out.F is then
 // F - F_Euler(ref) and out.W0 is W0 - ref (the FP64 reference parts are added in the cell
 // update).
-template <typename R, int DIM, bool WENO, bool VISC, bool DELTA = false>
+// NEED_F = false (used by the second MSMD stage, which needs only F_t and W_tt): the flux and
+// interface-value outputs F, W0 and the flux half of the bracket and of the non-equilibrium
+// branch are not computed (out.F = out.W0 = 0).
+template <typename R, int DIM, bool WENO, bool VISC, bool DELTA = false, bool NEED_F = true>
 __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, DIM>& in, double dt,
                                           PointOut<R, DIM>& out, const R* ref = nullptr,
                                           const R* d0 = nullptr) {
@@ -570,7 +573,10 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
   // W_xt = -(A W_xx + B W_xy), W_yt = -(A W_xy + B W_yy), W_tt = -(A W_xt + B W_yt), F_t = A W_t.
   R F[N], Ft[N], Wt[N], Wxt[N], Wyt[N], Wtt[N];
   R dW0[N];   // W0 - ref in the DELTA form
-  if (DELTA) {
+  if (!NEED_F) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) { F[k] = R(0); dW0[k] = R(0); }
+  } else if (DELTA) {
 #pragma unroll
     for (int k = 0; k < N; ++k) dW0[k] = WENO ? W0c[k] - ref[k] : d0[k];
     euler_flux_delta<R, DIM>(ref, dW0, gamma, F);
@@ -604,32 +610,28 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       // where rho<u psi A> = A_n W_t = F_t and rho<u psi a_tt> = A_n W_tt.
       R tau = fdiv<R>(R(P.mu), g0.p);
       R A[N], axt[N], ayt[N], att[N], Fvt[N];
-      maxw_solve<R, DIM>(g0, Wt, A);
+      if (NEED_F) maxw_solve<R, DIM>(g0, Wt, A);
       maxw_solve<R, DIM>(g0, Wxt, axt);
       maxw_solve<R, DIM>(g0, Wtt, att);
       if (DIM == 2) maxw_solve<R, DIM>(g0, Wyt, ayt);
       jac_n<R, DIM>(f, Wtt, Fvt);
-      R s = -tau * rho0;
       R Fb[N], Fbt[N];
-      gmul<R, DIM, false>(G20, a1, rho0, Fb);
+      if (NEED_F) gmul<R, DIM, false>(G20, a1, rho0, Fb);
       gmul<R, DIM, false>(G20, axt, rho0, Fbt);
       if (DIM == 2) {
-        gmul<R, DIM, true>(G11, a2, rho0, Fb);
+        if (NEED_F) gmul<R, DIM, true>(G11, a2, rho0, Fb);
         gmul<R, DIM, true>(G11, ayt, rho0, Fbt);
       }
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        F[k] += -tau * (Fb[k] + Ft[k]);
+        if (NEED_F) F[k] += -tau * (Fb[k] + Ft[k]);
         Ft[k] += -tau * (Fbt[k] + Fvt[k]);
       }
-      (void)s;
       if (P.Pr != 1.0) {
         // Prandtl-number fix (reading R10): (1/Pr - 1) q of the bracket terms.
         R fpr = R(1.0 / P.Pr - 1.0);
-        R q1 = -tau * heat_lin<R, DIM>(g0, a1, a2, A);
-        R q2 = -tau * heat_lin<R, DIM>(g0, axt, ayt, att);
-        F[N - 1] += fpr * q1;
-        Ft[N - 1] += fpr * q2;
+        if (NEED_F) F[N - 1] += fpr * (-tau * heat_lin<R, DIM>(g0, a1, a2, A));
+        Ft[N - 1] += fpr * (-tau * heat_lin<R, DIM>(g0, axt, ayt, att));
       }
     }
     if (WENO) {
@@ -674,7 +676,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       const R a0 = R(T.a0), a1 = R(T.a1), b0 = R(T.b0), b1 = R(T.b1);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        F[k] = F[k] + a0 * c0[k] + a1 * c1[k];
+        if (NEED_F) F[k] = F[k] + a0 * c0[k] + a1 * c1[k];
         Ft[k] = Ft[k] + b0 * c0[k] + b1 * c1[k];
       }
     }

@@ -18,7 +18,8 @@ template <int ORDER, bool WENO, bool VISC>
 static cudaError_t launch_1d32_t(const FaceArgs32& a, cudaStream_t s) {
   int threads = 128;
   int blocks = (a.nx + 1 + threads - 1) / threads;
-  faces_1d_f32_kernel<ORDER, WENO, VISC><<<blocks, threads, 0, s>>>(a);
+  if (a.stage == 1) faces_1d_f32_kernel<ORDER, WENO, VISC, 1><<<blocks, threads, 0, s>>>(a);
+  else faces_1d_f32_kernel<ORDER, WENO, VISC, 2><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -43,8 +44,11 @@ static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   const size_t shmem = T::smem_bytes(WENO);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT>,
+    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -52,7 +56,8 @@ static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + 1 + TA32 - 1) / TA32, (a.ny + T::TB - 1) / T::TB);
   else grid = dim3((a.nx + TA32 - 1) / TA32, (a.ny + 1 + T::TB - 1) / T::TB);
-  faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT><<<grid, block, shmem, s>>>(a);
+  if (a.stage == 1) faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1><<<grid, block, shmem, s>>>(a);
+  else faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -66,10 +66,11 @@ __device__ __forceinline__ void prefetch_line(const void* p) {
 // Start the epilogue's global reads of face `face` (stage 1: the FP64 states of its cells
 // cl, cr; stage 2: its FP64 flux part Xi and FP32 dLT) while the face is evaluated.
 template <int DIM, bool CG>
-__device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, long face, long nfaces, long cl, long cr) {
+__device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, int stage, long face, long nfaces,
+                                                       long cl, long cr) {
   const int N = DIM + 2;
   const long ncell = (long)a.nx * a.ny;
-  if (a.stage == 1) {
+  if (stage == 1) {
 #pragma unroll
     for (int v = 0; v < N; ++v) { prefetch_line<CG>(a.W + v * ncell + cl); prefetch_line<CG>(a.W + v * ncell + cr); }
   } else {
@@ -123,7 +124,8 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
 // exactly.  The dt/2 flux part only moves the intermediate state W*, so it stays in single
 // precision: across cell i its difference is A_{i+1/2} + D_{i-1/2}.  F, Ft, dW0, Wt, Wtt,
 // dFc in the global frame; cl, cr: the face's left and right cells.
-template <int DIM, int DIR, bool CG>
+// STAGE: 1 or 2 fixed at compile time, 0 read from a.stage.
+template <int DIM, int DIR, bool CG, int STAGE = 0>
 __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, long nfaces, long cl, long cr,
                                              const float* F, const float* Ft, const float* dW0,
                                              const float* Wt, const float* Wtt, const float* dFc) {
@@ -132,7 +134,8 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
   double* o64 = static_cast<double*>(a.out);
   float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
   const StepTimes* tc = a.tc;
-  if (a.stage == 1) {
+  const int stage = STAGE ? STAGE : a.stage;
+  if (stage == 1) {
     const float hf = ldf<CG>(&tc->hf), h2f = ldf<CG>(&tc->h2f), dtf = ldf<CG>(&tc->dtf), s6f = ldf<CG>(&tc->s6f);
     float dpsi[N];
 #pragma unroll
@@ -169,11 +172,13 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
 // ---------------------------------------------------------------------------
 // 1D FP32-bulk sweep: one thread per face f = 0..nx.
 // ---------------------------------------------------------------------------
-template <int ORDER, bool WENO, bool VISC, bool CG>
+// STAGE: 1 or 2 fixed at compile time (stage 2 needs only F_t and W_tt), 0 read from a.stage.
+template <int ORDER, bool WENO, bool VISC, bool CG, int STAGE = 0>
 __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
   const int N = 3;
   if (f > a.nx) return;
-  prefetch_face_epilogue<1, CG>(a, f, a.nx + 1, map_index(f - 1, a.nx, a.bcx), map_index(f, a.nx, a.bcx));
+  const int stage = STAGE ? STAGE : a.stage;
+  prefetch_face_epilogue<1, CG>(a, stage, f, a.nx + 1, map_index(f - 1, a.nx, a.bcx), map_index(f, a.nx, a.bcx));
   const double dt = ldd<CG>(a.dtp);
   const long ncell = a.nx;
   const long L = N * ncell;
@@ -208,16 +213,16 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
     pin.Wrx[v] = WENO ? rec[6][v] : rec[1][v];
   }
   PointOut<float, 1> po;
-  bool ok = gks_point<float, 1, WENO, VISC, true>(a.P, pin, dt, po, ref, d0);
+  bool ok = gks_point<float, 1, WENO, VISC, true, STAGE != 2>(a.P, pin, dt, po, ref, d0);
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
   float dFc[N] = {0.f, 0.f, 0.f};
-  if (a.stage == 1) euler_flux_delta<float, 1>(ref, dr, a.gammaf, dFc);
-  write_face32<1, 0, CG>(a, f, a.nx + 1, cref, map_index(f, a.nx, a.bcx), po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
+  if (stage == 1) euler_flux_delta<float, 1>(ref, dr, a.gammaf, dFc);
+  write_face32<1, 0, CG, STAGE>(a, f, a.nx + 1, cref, map_index(f, a.nx, a.bcx), po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
 }
 
-template <int ORDER, bool WENO, bool VISC>
+template <int ORDER, bool WENO, bool VISC, int STAGE>
 __global__ void __launch_bounds__(128) faces_1d_f32_kernel(FaceArgs32 a) {
-  sweep1d_f32_face<ORDER, WENO, VISC, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
+  sweep1d_f32_face<ORDER, WENO, VISC, false, STAGE>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,8 +248,9 @@ struct Tile32 {
 // One tile of TA32 x TB32 faces; tid = linear thread index in a block of TA32 * TB32 threads;
 // (bx, by) = tile coordinates (the block indices of the standalone launch); smf = dynamic
 // shared memory of (NQ + 2) * 4 * NS floats.
-template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1>
+template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1, int STAGE = 0>
 __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, int by, int tid, float* smf) {
+  const int stage = STAGE ? STAGE : a.stage;
   const int N = 4;
   const int NQ = WENO ? 7 : 3;
   typedef Tile32<DIR, FPT> T;
@@ -297,7 +303,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
       // F_Euler(W_right) - F_Euler(W_ref) of the face's two cells, in the face's frame
       // only the tile's own face rows (not the tangential halo) use it
       const bool own = DIR == 0 ? (sb >= 2 && sb < T::TB + 2) : (sa >= 2 && sa < TA32 + 2);
-      if (a.stage == 1 && own) euler_flux_delta<float, 2>(ref, dr, a.gammaf, dfc);
+      if (stage == 1 && own) euler_flux_delta<float, 2>(ref, dr, a.gammaf, dfc);
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q)
@@ -332,7 +338,7 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
                              : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
     const long pr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
                              : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
-    prefetch_face_epilogue<2, CG>(a, pf, pn, pl, pr);
+    prefetch_face_epilogue<2, CG>(a, stage, pf, pn, pl, pr);
   }
   int slot[5];
 #pragma unroll
@@ -390,12 +396,12 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
       }
     }
     PointOut<float, 2> po;
-    ok &= gks_point<float, 2, WENO, VISC, true>(a.P, pin, dt, po, ref, d0);
+    ok &= gks_point<float, 2, WENO, VISC, true, STAGE != 2>(a.P, pin, dt, po, ref, d0);
     const float wg = GWf[g];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      F[v] += wg * po.F[v]; Ft[v] += wg * po.Ft[v];
-      dW0[v] += wg * po.W0[v]; Wt[v] += wg * po.Wt[v]; Wtt[v] += wg * po.Wtt[v];
+      Ft[v] += wg * po.Ft[v]; Wtt[v] += wg * po.Wtt[v];
+      if (STAGE != 2) { F[v] += wg * po.F[v]; dW0[v] += wg * po.W0[v]; Wt[v] += wg * po.Wt[v]; }
     }
   }
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
@@ -413,15 +419,15 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
                            : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
   const long cr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
                            : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
-  write_face32<2, DIR, CG>(a, face, nfaces, cl, cr, F, Ft, dW0, Wt, Wtt, dFc);
+  write_face32<2, DIR, CG, STAGE>(a, face, nfaces, cl, cr, F, Ft, dW0, Wt, Wtt, dFc);
   }
 }
 
 // Linear Euler tiles fit 128 registers without spilling: four blocks (16 warps) per SM.
-template <int ORDER, bool WENO, bool VISC, int DIR, int FPT>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE>
 __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 4) faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
 }
 
 // ---------------------------------------------------------------------------
@@ -579,13 +585,13 @@ __global__ void __launch_bounds__(256) update_f32_kernel(UpdateArgs32 a) {
 // batch kernel's size and register allocation stay bounded instead of inlining every
 // variant.  The standalone kernels inline the same bodies; the compiler may contract
 // multiply-adds differently in the two, so the two agree to single-precision rounding.
-template <int ORDER, bool WENO, bool VISC>
+template <int ORDER, bool WENO, bool VISC, int STAGE>
 __device__ __noinline__ void sweep1d_f32_face_call(const FaceArgs32& a, int f) {
-  sweep1d_f32_face<ORDER, WENO, VISC, true>(a, f);
+  sweep1d_f32_face<ORDER, WENO, VISC, true, STAGE>(a, f);
 }
-template <int ORDER, bool WENO, bool VISC, int DIR, int FPT>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE>
 __device__ __noinline__ void sweep2d_f32_tile_call(const FaceArgs32& a, int bx, int by, int tid, float* smf) {
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, true, FPT>(a, bx, by, tid, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, true, FPT, STAGE>(a, bx, by, tid, smf);
 }
 template <int DIM, int STAGE>
 __device__ __noinline__ void update_f32_cell_call(const UpdateArgs32& a, long c) {
