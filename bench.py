@@ -52,12 +52,12 @@ KERNEL_MODEL = {
     ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1910.2},
     ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1910.2},
     ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1910.2},
-    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2164.1, "f64": 35.0, "traffic": 157.6},
-    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2073.5, "f64": 35.0, "traffic": 161.5},
+    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2156.1, "f64": 35.0, "traffic": 158.0},
+    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2076.5, "f64": 35.0, "traffic": 161.5},
     ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 250.1},
-    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 2052.1, "f64": 4.0, "traffic": 108.2},
-    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1961.5, "f64": 4.0, "traffic": 109.3},
-    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 345.0},
+    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0},
+    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.4},
+    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 345.1},
 }
 HBM_FALLBACK_GBS = 6800.0
 
