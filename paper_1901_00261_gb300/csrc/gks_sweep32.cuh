@@ -579,7 +579,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
 }
 
 template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256) update_f32_kernel(UpdateArgs32 a) {
+__global__ void __launch_bounds__(256, 3) update_f32_kernel(UpdateArgs32 a) {
   update_f32_cell<DIM, STAGE, false>(a, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
