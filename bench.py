@@ -138,6 +138,26 @@ def dist_env():
     return ws, rank, local
 
 
+# Replica timing over ranks (one process per GPU, each advancing its own problems; no data
+# exchange between ranks): the job's time is the slowest rank's, its work the sum of all
+# ranks' work.  dist is torch.distributed (or None for one process); device holds the
+# reduction tensor ("cuda" under NCCL, "cpu" under gloo).
+def reduce_over_ranks(value, dist, device, op="max"):
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_per_rank, steps, dist, device):
+    """Units per second of the whole job: all ranks' units over the slowest rank's time."""
+    units = reduce_over_ranks(units_per_rank, dist, device, "sum")
+    ms = reduce_over_ranks(ms_per_rank, dist, device, "max")
+    return units * steps / (ms * 1e-3), ms
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -284,6 +304,10 @@ def run_batch(args, ws, rank, local):
     import numpy as np
     import torch
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     from paper_1901_00261_gb300 import gks
     stream = torch.cuda.Stream()     # the batch runs on this stream; the events are recorded on it
     B = gks.Batch(states, stream=stream.cuda_stream)
@@ -301,18 +325,22 @@ def run_batch(args, ws, rank, local):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     with ClockSampler(local) as clk:
         t0.record(stream)
         B.steps(dts, args.steps)
         t1.record(stream)
         torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     B.sync()      # raises if any kept problem failed inside the timed region
-    ms = t0.elapsed_time(t1)
     cells = sum(st.nx * st.ny for st in states)
+    value, ms = job_throughput(cells, t0.elapsed_time(t1), args.steps, dist, "cuda")
     if rank == 0:
         fpt, bps = B.config()
         line = {"metric": "cell-updates/s (batched mixed problems, FP32-bulk, persistent launch)",
-                "value": cells * args.steps * ws / (ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+                "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-bulk (f64 time coefficients and accumulation)", "data": "synthetic",
@@ -329,6 +357,8 @@ def run_batch(args, ws, rank, local):
                 "autotune": report.strip().splitlines()}
         print(json.dumps(line), flush=True)
     B.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -386,17 +416,13 @@ def main():
             t1.record(stream)
             torch.cuda.synchronize()
         barrier()
-        ms = t0.elapsed_time(t1)
         G.sync()
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        value, ms = job_throughput(ncell, t0.elapsed_time(t1), args.steps, dist, "cuda")
         per_launch = kernel_ms / args.steps
         k_dom = int(np.argmax(per_launch))
         name = slot_names[k_dom]
         roof = roofline(form, name, float(per_launch[k_dom]), st.nx, st.ny, args.order, peak64, peak32)
-        r = {"value": ncell * args.steps * ws / (ms * 1e-3), "ms_per_step": ms / args.steps,
+        r = {"value": value, "ms_per_step": ms / args.steps,
              "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
              "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}
         if not args.no_acc and rank == 0:
