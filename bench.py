@@ -113,7 +113,7 @@ def roofline(form, name, ms, nx, ny, order, peak64, peak32):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
     ap.add_argument("--n", type=int, default=None,
@@ -159,7 +159,7 @@ def job_throughput(units_per_rank, ms_per_rank, steps, dist, device):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -172,7 +172,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -252,11 +252,13 @@ def run_reference(args, ws, rank):
     p = 0.4 * (st.W[3] - 0.5 * rho * (U * U + V * V))
     c = np.sqrt(1.4 * p / rho)
     dt = CFL / ((np.abs(U) + c) / st.dx + (np.abs(V) + c) / st.dy).max()
+    # each step is a bounded sample (about two minutes for the whole run)
+    budget = max(0.5, min(8.0, 120.0 / max(1, args.steps)))
     per_step = []
     for _ in range(args.warmup):
-        cpu_baseline(st, dt, budget_s=2.0, window=64)
+        cpu_baseline(st, dt, budget_s=min(2.0, budget), window=64)
     for _ in range(args.steps):
-        per_step.append(cpu_baseline(st, dt, budget_s=8.0, window=96))
+        per_step.append(cpu_baseline(st, dt, budget_s=budget, window=96))
     val = statistics.median([r["value"] for r in per_step])
     cb = dict(per_step[-1])
     cb["value"] = val
