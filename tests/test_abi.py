@@ -67,3 +67,34 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gks._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         gks.lib(build_if_missing=False)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (dict(nx=4), "nx >= 5"),
+    (dict(ny=3), "ny == 1 or ny >= 5"),
+    (dict(order=7), "order"),
+    (dict(recon=2), "recon"),
+    (dict(gamma=1.0), "physics or domain"),
+    (dict(x1=0.0), "physics or domain"),
+    (dict(bc_x=2), "bc"),
+])
+def test_batch_create_rejects_invalid_problems(mutate, msg):
+    """Problem validation happens before any device work, so it is checked here without a GPU;
+    the offending problem is named by index."""
+    L = gks.lib()
+    good = dict(nx=64, ny=1, order=8, recon=1, gamma=1.4, mu=0.0, Pr=1.0,
+                x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=1, bc_y=1)
+    bad = dict(good, **mutate)
+    arr = (gks.Problem * 2)()
+    for k, d in enumerate((good, bad)):
+        arr[k] = gks.Problem(d["nx"], d["ny"], d["order"], d["recon"], d["gamma"], d["mu"], d["Pr"],
+                             d["x0"], d["x1"], d["y0"], d["y1"], d["bc_x"], d["bc_y"])
+    assert not L.gks_batch_create(2, arr, None)
+    err = L.gks_batch_last_error().decode()
+    assert "problem 1" in err and msg in err
+
+
+def test_batch_create_rejects_empty_list():
+    L = gks.lib()
+    assert not L.gks_batch_create(0, None, None)
+    assert "n >= 1" in L.gks_batch_last_error().decode()
