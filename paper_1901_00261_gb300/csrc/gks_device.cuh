@@ -642,11 +642,10 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       const R theta = (P.mu > 0.0 ? fdiv<R>(R(P.mu), g0.p * R(dt)) : R(P.eps_tau)) +
                       R(P.C_tau) * fabs(fdiv<R>(pl - pr, pl + pr));
       const TimeCoef T = time_coefs((double)theta, (double)fdiv<R>(R(0.5), theta), dt);
+      // c0 starts from minus the collisionless flux of g0 (F_Euler(W0); the bracket is not
+      // part of it), formed here so that it does not depend on F being computed
       R c0[N], c1[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) c0[k] = -F[k];
-      if (VISC || DELTA) {
-        // c0 needs the collisionless flux of g0 only (the bracket is not part of it)
+      {
         R m = W0c[1];
         c0[0] = -m; c0[1] = -(m * f.U + f.p);
         if (DIM == 2) c0[2] = -m * f.V;

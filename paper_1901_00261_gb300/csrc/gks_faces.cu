@@ -49,7 +49,8 @@ __device__ __forceinline__ void write_face(double* out, long face, long nfaces, 
 // ---------------------------------------------------------------------------
 // 1D: one thread per face f = 0..nx (face f at x_{f-1/2}).
 // ---------------------------------------------------------------------------
-template <int ORDER, bool WENO, bool VISC>
+// STAGE (1 or 2): the second MSMD stage needs only F_t and W_tt of each face.
+template <int ORDER, bool WENO, bool VISC, int STAGE>
 __global__ void __launch_bounds__(128) faces_1d_kernel(FaceArgs a) {
   typedef double R;
   const int N = 3;
@@ -79,9 +80,9 @@ __global__ void __launch_bounds__(128) faces_1d_kernel(FaceArgs a) {
     pin.Wrx[v] = WENO ? rec[6][v] : rec[1][v];
   }
   PointOut<R, 1> po;
-  bool ok = gks_point<R, 1, WENO, VISC>(a.P, pin, dt, po);
+  bool ok = gks_point<R, 1, WENO, VISC, false, STAGE != 2>(a.P, pin, dt, po);
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
-  write_face<1>(a.out, f, a.nx + 1, a.stage, dt, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
+  write_face<1>(a.out, f, a.nx + 1, STAGE, dt, po.F, po.Ft, po.W0, po.Wt, po.Wtt);
 }
 
 // ---------------------------------------------------------------------------
@@ -101,7 +102,7 @@ struct Tile {
   static constexpr int NS = SA * SB;
 };
 
-template <int ORDER, bool WENO, bool VISC, int DIR>
+template <int ORDER, bool WENO, bool VISC, int DIR, int STAGE>
 __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   typedef double R;
   const int N = 4;
@@ -199,12 +200,12 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
       }
     }
     PointOut<R, 2> po;
-    ok &= gks_point<R, 2, WENO, VISC>(a.P, pin, dt, po);
+    ok &= gks_point<R, 2, WENO, VISC, false, STAGE != 2>(a.P, pin, dt, po);
     const double wg = GW[g];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      F[v] += wg * po.F[v]; Ft[v] += wg * po.Ft[v];
-      W0[v] += wg * po.W0[v]; Wt[v] += wg * po.Wt[v]; Wtt[v] += wg * po.Wtt[v];
+      Ft[v] += wg * po.Ft[v]; Wtt[v] += wg * po.Wtt[v];
+      if (STAGE != 2) { F[v] += wg * po.F[v]; W0[v] += wg * po.W0[v]; Wt[v] += wg * po.Wt[v]; }
     }
   }
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   long face, nfaces;
   if (DIR == 0) { face = (long)ct * (a.nx + 1) + fn; nfaces = (long)a.ny * (a.nx + 1); }
   else { face = (long)fn * a.nx + ct; nfaces = (long)(a.ny + 1) * a.nx; }
-  write_face<2>(a.out, face, nfaces, a.stage, dt, F, Ft, W0, Wt, Wtt);
+  write_face<2>(a.out, face, nfaces, STAGE, dt, F, Ft, W0, Wt, Wtt);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,7 +223,8 @@ template <int ORDER, bool WENO, bool VISC>
 static cudaError_t launch_1d_t(const FaceArgs& a, cudaStream_t s) {
   int threads = 128;
   int blocks = (a.nx + 1 + threads - 1) / threads;
-  faces_1d_kernel<ORDER, WENO, VISC><<<blocks, threads, 0, s>>>(a);
+  if (a.stage == 1) faces_1d_kernel<ORDER, WENO, VISC, 1><<<blocks, threads, 0, s>>>(a);
+  else faces_1d_kernel<ORDER, WENO, VISC, 2><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -242,8 +244,11 @@ static cudaError_t launch_2d_t(const FaceArgs& a, cudaStream_t s) {
   size_t shmem = sizeof(double) * NQ * 4 * T::NS;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_kernel<ORDER, WENO, VISC, DIR>,
+    cudaError_t e = cudaFuncSetAttribute(faces_2d_kernel<ORDER, WENO, VISC, DIR, 1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(faces_2d_kernel<ORDER, WENO, VISC, DIR, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -251,7 +256,8 @@ static cudaError_t launch_2d_t(const FaceArgs& a, cudaStream_t s) {
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + 1 + TA - 1) / TA, (a.ny + TB - 1) / TB);
   else grid = dim3((a.nx + TA - 1) / TA, (a.ny + 1 + TB - 1) / TB);
-  faces_2d_kernel<ORDER, WENO, VISC, DIR><<<grid, block, shmem, s>>>(a);
+  if (a.stage == 1) faces_2d_kernel<ORDER, WENO, VISC, DIR, 1><<<grid, block, shmem, s>>>(a);
+  else faces_2d_kernel<ORDER, WENO, VISC, DIR, 2><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
 }
 

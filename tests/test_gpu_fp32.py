@@ -164,6 +164,27 @@ def test_fp32_bulk_sod_against_exact():
     assert e[gks.PREC_FP32_BULK] <= 1.05 * e[gks.PREC_FP64], e
 
 
+def test_fp32_bulk_full_size_vortex_step():
+    """The benchmark configuration itself (2048^2, 8th order, linear, the same launches): one
+    FP32-bulk step over the whole grid against the FP64 step within the 2D linear per-step bounds
+    (W 3e-8, slopes 3e-7 of max|W|/h), and conservation to FP64 rounding."""
+    st = inputs.isentropic_vortex_2d(2048, order=8)
+    A = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
+    dt = 0.3 / A.max_wavespeed()
+    A.step(dt)
+    a = A.get_state()
+    A.close()
+    B = gks.Solver.from_state(st, precision=gks.PREC_FP64)
+    B.step(dt)
+    b = B.get_state()
+    B.close()
+    assert rel(a[0], b[0]) <= 3e-8
+    for k, h in ((1, st.dx), (2, st.dy)):
+        assert rel(a[k], b[k], [np.abs(b[0][v]).max() / h for v in range(4)]) <= 3e-7
+    m0 = st.W.sum(axis=(1, 2))
+    assert np.abs(a[0].sum(axis=(1, 2)) - m0).max() <= 1e-12 * np.abs(st.W).sum(axis=(1, 2)).max()
+
+
 def test_fp32_bulk_set_state_refreshes_mirror():
     st = inputs.isentropic_vortex_2d(48, order=8)
     A = gks.Solver.from_state(st, precision=gks.PREC_FP32_BULK)
