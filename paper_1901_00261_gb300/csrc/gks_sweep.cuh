@@ -6,7 +6,13 @@
 namespace gks {
 
 __device__ __forceinline__ int map_index(int i, int n, int bc) {
-  if (bc == 0) { i %= n; return i < 0 ? i + n : i; }
+  if (bc == 0) {
+    // indices lie within a few cells of [0, n): one add or subtract; the remainder only for
+    // the far halo of grids smaller than a tile
+    if (i >= n) { i -= n; if (i >= n) i %= n; }
+    else if (i < 0) { i += n; if (i < 0) { i %= n; if (i < 0) i += n; } }
+    return i;
+  }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 

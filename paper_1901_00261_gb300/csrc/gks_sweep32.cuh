@@ -423,10 +423,11 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   }
 }
 
-// Linear Euler tiles: at least four blocks (16 warps) per SM, five for the lighter second
-// stage (both measured fastest); the WENO-Z / viscous tiles are left to the compiler.
+// Linear Euler tiles: five blocks (20 warps) per SM, measured fastest for both stages (the
+// first stage spills a few bytes at that bound); the WENO-Z / viscous tiles are left to the
+// compiler.
 template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE>
-__global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : (STAGE == 2 ? 5 : 4))
+__global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 5)
 faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
   sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
