@@ -61,11 +61,15 @@ typedef struct gks_opts {
   double eps_tau, C_tau;   /* numerical collision time eps*dt + C|pl-pr|/(pl+pr) dt of Sec. 4;
                               defaults 0.01 and 1 */
   int use_graph;           /* 1: replay the two-stage step as a captured CUDA graph */
+  int tau_mode;            /* collision time of the Chapman-Enskog terms: 0 (default) mu/p,
+                              the physical time; 1 the numerical time above (mu/p, or eps*dt
+                              for mu = 0, plus the pressure-jump term of the WENO-Z states),
+                              i.e. the same tau in the bracket and the exponentials */
   void* stream;            /* cudaStream_t to run on; NULL: the library creates one */
 } gks_opts;
 
 /* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-12,
- * eps_tau 0.01, C_tau 1, use_graph 1, stream NULL. */
+ * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL. */
 void gks_default_opts(gks_opts* o);
 
 /* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio;

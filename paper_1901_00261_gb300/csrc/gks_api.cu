@@ -75,7 +75,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     fa.M = c->mirror;
     fa.W = c->state;
     fa.dnf = (float)c->dx; fa.gammaf = (float)c->P.gamma; fa.epsf = (float)c->P.weno_eps;
-    const bool visc = c->P.mu > 0.0;
+    const bool visc = c->P.mu > 0.0 || c->P.tau_mode == 1;
     gks::UpdateArgs32 ua;
     ua.fx = reinterpret_cast<float*>(c->fx); ua.fy = reinterpret_cast<float*>(c->fy);
     ua.W = c->state; ua.M = c->mirror;
@@ -109,7 +109,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
   fa.dtp = c->d_dt; fa.status = c->d_status;
   fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
   fa.P = c->P;
-  const bool visc = c->P.mu > 0.0;
+  const bool visc = c->P.mu > 0.0 || c->P.tau_mode == 1;
   const long L = state_len(c);
   gks::UpdateArgs ua;
   ua.fx = c->fx; ua.fy = c->fy; ua.acc = c->acc;
@@ -172,6 +172,7 @@ void gks_default_opts(gks_opts* o) {
   o->weno_eps = 1e-12;
   o->eps_tau = 0.01; o->C_tau = 1.0;
   o->use_graph = 1;
+  o->tau_mode = 0;
   o->stream = nullptr;
 }
 
@@ -193,6 +194,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   if ((o.bc_x != 0 && o.bc_x != 1) || (o.bc_y != 0 && o.bc_y != 1)) { fail(GKS_EINVAL, "bc must be 0 or 1%s"); return nullptr; }
   if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_FP32_BULK) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
+  if (o.tau_mode != 0 && o.tau_mode != 1) { fail(GKS_EINVAL, "tau_mode must be 0 or 1%s"); return nullptr; }
 
   gks_ctx* c = new (std::nothrow) gks_ctx();
   if (!c) { fail(GKS_ENOMEM, "host allocation failed%s"); return nullptr; }
@@ -205,6 +207,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   c->P.K = c->dim == 1 ? (3.0 - gamma) / (gamma - 1.0) : (4.0 - 2.0 * gamma) / (gamma - 1.0);
   c->P.mu = mu; c->P.Pr = Pr;
   c->P.eps_tau = o.eps_tau; c->P.C_tau = o.C_tau; c->P.weno_eps = o.weno_eps;
+  c->P.tau_mode = o.tau_mode;
   gks::set_phys_floats(c->P);
 
   cudaError_t e;

@@ -427,7 +427,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     memset(&P, 0, sizeof(P));
     P.dim = dim; P.order = q.order; P.recon = q.recon;
     const double dx = (q.x1 - q.x0) / q.nx, dy = dim == 2 ? (q.y1 - q.y0) / q.ny : 1.0;
-    gks::PhysParams ph;
+    gks::PhysParams ph{};
     ph.gamma = q.gamma;
     ph.K = dim == 1 ? (3.0 - q.gamma) / (q.gamma - 1.0) : (4.0 - 2.0 * q.gamma) / (q.gamma - 1.0);
     ph.mu = q.mu; ph.Pr = q.Pr; ph.eps_tau = 0.01; ph.C_tau = 1.0; ph.weno_eps = 1e-12;

@@ -390,6 +390,7 @@ __device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt
 struct PhysParams {
   double gamma, K, mu, Pr, eps_tau, C_tau, weno_eps;
   float gammaf, Kf;   // single-precision copies of gamma and K (set with set_phys_floats)
+  int tau_mode = 0;   // 0: bracket with mu/p (reading R1); 1: bracket with the numerical time
 };
 
 inline void set_phys_floats(PhysParams& P) { P.gammaf = (float)P.gamma; P.Kf = (float)P.K; }
@@ -608,7 +609,14 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       // Chapman-Enskog bracket with the physical collision time mu/p (reading R1):
       // -tau rho<u psi (a1 u + a2 v + A)> and -tau rho<u psi (a_xt u + a_yt v + a_tt)>,
       // where rho<u psi A> = A_n W_t = F_t and rho<u psi a_tt> = A_n W_tt.
+      // tau_mode 1 takes the numerical time of Sec. 4 instead: mu/p, or eps dt for the Euler
+      // equations, plus C |pl - pr| / (pl + pr) dt (zero for the linear reconstruction,
+      // whose two sides are one state).
       R tau = fdiv<R>(R(P.mu), g0.p);
+      if (P.tau_mode == 1) {
+        if (!(P.mu > 0.0)) tau = R(P.eps_tau) * R(dt);
+        if (WENO) tau += R(P.C_tau) * fabs(fdiv<R>(pl - pr, pl + pr)) * R(dt);
+      }
       R A[N], axt[N], ayt[N], att[N], Fvt[N];
       if (NEED_F) maxw_solve<R, DIM>(g0, Wt, A);
       maxw_solve<R, DIM>(g0, Wxt, axt);

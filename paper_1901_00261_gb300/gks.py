@@ -37,6 +37,7 @@ class Opts(ctypes.Structure):
                 ("weno_eps", ctypes.c_double),
                 ("eps_tau", ctypes.c_double), ("C_tau", ctypes.c_double),
                 ("use_graph", ctypes.c_int),
+                ("tau_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -150,7 +151,8 @@ class Solver:
                  order: int = 6, recon: int = RECON_LINEAR, x0: float = 0.0, x1: float = 1.0,
                  y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
                  weno_eps: float = 1e-12, use_graph: bool = True, stream=None,
-                 precision: int = PREC_FP64):
+                 precision: int = PREC_FP64, tau_mode: int = 0, eps_tau: float = 0.01,
+                 C_tau: float = 1.0):
         L = lib()
         o = default_opts()
         o.precision = precision
@@ -158,6 +160,8 @@ class Solver:
         o.bc_x, o.bc_y = bc_x, bc_y
         o.weno_eps = weno_eps
         o.use_graph = 1 if use_graph else 0
+        o.tau_mode = tau_mode
+        o.eps_tau, o.C_tau = eps_tau, C_tau
         o.stream = stream
         self._h = L.gks_create(nx, ny, gamma, mu, Pr, order, recon, ctypes.byref(o))
         if not self._h:

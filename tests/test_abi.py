@@ -36,6 +36,15 @@ def test_library_exports_every_declared_symbol():
 def test_default_opts():
     o = gks.default_opts()
     assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-12, 0.01, 1.0, 1)
+    assert o.tau_mode == 0 and o.stream is None
+
+
+def test_create_rejects_invalid_tau_mode():
+    L = gks.lib()
+    o = gks.default_opts()
+    o.tau_mode = 2
+    assert not L.gks_create(10, 1, 1.4, 0.0, 1.0, 6, 0, ctypes.byref(o))
+    assert "tau_mode" in gks.last_error()
 
 
 @pytest.mark.parametrize("args,msg", [

@@ -163,6 +163,60 @@ def test_2d_transmissive_boundaries():
     one_step_parity(st)
 
 
+# ------------------------------------------------------------- tau_mode = 1
+# The literal reading of Sec. 4: the numerical collision time (mu/p, or eps*dt for the Euler
+# equations, plus the pressure-jump term of the two WENO-Z states) in the Chapman-Enskog
+# terms as well as in the exponentials.  Compared with the oracle run in the same mode, and
+# checked to differ from the default mode (so that the option is exercised).
+TAU_CASES = [
+    ("linear 2D 8th vortex, Euler", lambda: inputs.isentropic_vortex_2d(40, order=8, recon=0, ny=36), 2),
+    ("WENO-Z 1D 8th Sod, Euler", lambda: inputs.sod_1d(400, order=8, recon=1), 2),
+    ("WENO-Z 2D 6th vortex, Euler", lambda: inputs.isentropic_vortex_2d(40, order=6, recon=1, ny=36), 2),
+    ("WENO-Z 2D NS shear layer", lambda: inputs.shear_layer_2d(48, seed=0), 2),
+]
+
+
+def _oracle_of(st, tau_mode):
+    O = oracle.Solver(st.nx, st.ny, st.gamma, st.mu, st.Pr, st.order, st.recon, st.bc_x, st.bc_y,
+                      st.x0, st.x1, st.y0, st.y1, tau_mode=tau_mode)
+    O.set_state(st.W, st.Wx, st.Wy)
+    return O
+
+
+@pytest.mark.parametrize("name,make,nsteps", TAU_CASES, ids=[c[0] for c in TAU_CASES])
+def test_tau_mode_numerical_time_in_bracket(name, make, nsteps):
+    st = make()
+    G = gks.Solver.from_state(st, tau_mode=1)
+    O1, O0 = _oracle_of(st, 1), _oracle_of(st, 0)
+    dt = cfl_dt(O1)
+    for _ in range(nsteps):
+        G.step(dt)
+        O1.step(dt)
+        O0.step(dt)
+    assert_parity(G, O1, what=name, dx=st.dx, dy=st.dy)
+    assert rel_err(O0.get_state()[0], O1.get_state()[0]) > 1e3 * TOL, name
+
+
+@pytest.mark.parametrize("name,make,nsteps,tolw,tols", [
+    ("linear 2D 8th vortex, Euler", lambda: inputs.isentropic_vortex_2d(64, order=8, recon=0), 1, 3e-8, 3e-7),
+    ("WENO-Z 1D 8th Sod, Euler", lambda: inputs.sod_1d(1000, order=8, recon=1), 1, 2e-6, 2e-6),
+], ids=["fp32 linear vortex", "fp32 weno sod"])
+def test_tau_mode_fp32_bulk(name, make, nsteps, tolw, tols):
+    # FP32-bulk form in the same mode, within the bounds of its comparison with FP64
+    st = make()
+    G = gks.Solver.from_state(st, tau_mode=1, precision=gks.PREC_FP32_BULK)
+    O = _oracle_of(st, 1)
+    dt = cfl_dt(O)
+    for _ in range(nsteps):
+        G.step(dt)
+        O.step(dt)
+    g, o = G.get_state(), O.get_state()
+    assert rel_err(g[0], o[0]) <= tolw, name
+    for k, h in ((1, st.dx), (2, st.dy)):
+        if o[k] is not None:
+            assert rel_err(g[k], o[k], slope_floor(o[0], h)) <= tols, name
+
+
 def test_2d_graph_and_plain_launches_agree_bitwise():
     st = inputs.isentropic_vortex_2d(40, order=8, recon=0)
     A = gks.Solver.from_state(st, use_graph=True)
