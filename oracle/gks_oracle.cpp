@@ -56,6 +56,12 @@
 //   R11 1D internal degrees of freedom K = (3 - gamma)/(gamma - 1).
 //   R12 the Maxwellian exponent is negative.
 //   R14 transmissive boundary: ghost cells copy the boundary cell's W and slopes.
+//   R24 reflecting wall (bc 2; the blast-wave and double-Mach walls of Sec. 5): ghost
+//       cell k outside the wall is the mirror image of the cell at the same distance
+//       inside.  The momentum normal to the wall changes sign; so does the derivative
+//       normal to the wall of every other variable (even functions across the mirror have
+//       odd derivatives), while the normal momentum's normal derivative keeps its sign.
+//       Derivatives along the wall keep the sign of their variable.
 //   R23 the equilibrium state g0 takes its value from the collision of the two initial
 //       states, W0 = int_{u>0} psi g_l + int_{u<0} psi g_r (identical to the linear
 //       reconstruction when the scheme is linear), and its derivatives from the compact
@@ -663,13 +669,43 @@ inline long cidx(const Solver& S, int v, int j, int i) { return ((long)v * S.ny 
 
 int map_index(int i, int n, int bc) {
   if (bc == 0) { i %= n; if (i < 0) i += n; return i; }
+  if (bc == 2) {
+    // mirror about the wall: cell -1 is cell 0, cell n is cell n - 1, ...
+    if (i < 0) i = -1 - i;
+    if (i >= n) i = 2 * n - 1 - i;
+    return i;
+  }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// True when index i lies beyond a reflecting wall (its cell is a mirror image, R24).
+bool is_mirror(int i, int n, int bc) { return bc == 2 && (i < 0 || i >= n); }
+
+// Mirror image of a ghost cell across a wall normal to axis `axis` (1 = x, 2 = y; the
+// momentum component with that index changes sign), for a stencil running across the
+// wall.  w: conservative values; d: their derivatives along the stencil (wall-normal)
+// direction, which change sign except that of the normal momentum.
+void mirror_cell(int n, int axis, double* w, double* d) {
+  w[axis] = -w[axis];
+  for (int v = 0; v < n; ++v)
+    if (v != axis) d[v] = -d[v];
 }
 
 // Normal reconstruction at one face from a 4-cell row (Secs. 3.1, 3.3).
 // in8[v][m] stencil inputs per conservative variable; h = cell size.
 // Outputs are line averages over the face: W0, dW0/dn, d2W0/dn2, Wl, dWl/dn, Wr, dWr/dn.
 struct FaceRecon { double W0[4], W0n[4], W0nn[4], Wl[4], Wln[4], Wr[4], Wrn[4]; };
+
+// Face line-averages of a face row beyond a reflecting wall parallel to the face normal
+// (R24): the mirror image of the row inside.  The wall-normal momentum is component 2 of
+// the face's frame (the tangential velocity) and changes sign in every quantity; the
+// derivatives across the face are tangential to the wall and keep their variable's sign.
+FaceRecon mirror_tangential(const FaceRecon& r) {
+  FaceRecon m = r;
+  double* q[7] = {m.W0, m.W0n, m.W0nn, m.Wl, m.Wln, m.Wr, m.Wrn};
+  for (double* a : q) a[2] = -a[2];
+  return m;
+}
 
 // Returns false when the state the characteristic projection is taken at is not physical
 // (rho <= 0 or p <= 0): the eigenvectors do not exist there.
@@ -743,12 +779,13 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
   for (long idx = 0; idx < (long)(nx + 1) * ny; ++idx) {
     int f = (int)(idx % (nx + 1)), j = (int)(idx / (nx + 1));
     double in8[4][8];
-    for (int v = 0; v < n; ++v)
-      for (int o = 0; o < 4; ++o) {
-        int ci = map_index(f - 2 + o, nx, S.bcx);
-        in8[v][o] = W[cidx(S, v, j, ci)];
-        in8[v][4 + o] = S.dx * Wx[cidx(S, v, j, ci)];
-      }
+    for (int o = 0; o < 4; ++o) {
+      int ci = map_index(f - 2 + o, nx, S.bcx);
+      double w[4], wx[4];
+      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, j, ci)]; wx[v] = Wx[cidx(S, v, j, ci)]; }
+      if (is_mirror(f - 2 + o, nx, S.bcx)) mirror_cell(n, 1, w, wx);
+      for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dx * wx[v]; }
+    }
     if (!normal_recon(S, in8, S.dx, rx[idx])) {
 #pragma omp critical
       ok = false;
@@ -773,7 +810,11 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       } else {
         wgt = T.gauss_w[g];
         const FaceRecon* rr[5];
-        for (int t = 0; t < 5; ++t) rr[t] = &rx[(size_t)map_index(j - 2 + t, ny, S.bcy) * (nx + 1) + f];
+        FaceRecon mir[5];
+        for (int t = 0; t < 5; ++t) {
+          rr[t] = &rx[(size_t)map_index(j - 2 + t, ny, S.bcy) * (nx + 1) + f];
+          if (is_mirror(j - 2 + t, ny, S.bcy)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
+        }
         const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
         for (int v = 0; v < n; ++v) {
           for (int t = 0; t < 5; ++t) {
@@ -814,6 +855,7 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       int cj = map_index(f - 2 + o, ny, S.bcy);
       double w[4], wy[4];
       for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, cj, i)]; wy[v] = Wy[cidx(S, v, cj, i)]; }
+      if (is_mirror(f - 2 + o, ny, S.bcy)) mirror_cell(n, 2, w, wy);
       swapuv(dim, w); swapuv(dim, wy);
       for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dy * wy[v]; }
     }
@@ -832,7 +874,11 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       PointIn pin; std::memset(&pin, 0, sizeof(pin));
       double wgt = T.gauss_w[g];
       const FaceRecon* rr[5];
-      for (int t = 0; t < 5; ++t) rr[t] = &ry[(size_t)f * nx + map_index(i - 2 + t, nx, S.bcx)];
+      FaceRecon mir[5];
+      for (int t = 0; t < 5; ++t) {
+        rr[t] = &ry[(size_t)f * nx + map_index(i - 2 + t, nx, S.bcx)];
+        if (is_mirror(i - 2 + t, nx, S.bcx)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
+      }
       const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
       for (int v = 0; v < n; ++v)
         for (int t = 0; t < 5; ++t) {
@@ -1054,6 +1100,7 @@ void* orc_create(int nx, int ny, double gamma, double mu, double Pr, int order, 
   if (recon != 0 && recon != 1) return nullptr;
   if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return nullptr;
   if (!(x1 > x0) || (ny > 1 && !(y1 > y0))) return nullptr;
+  if (bc_x < 0 || bc_x > 2 || bc_y < 0 || bc_y > 2) return nullptr;
   Solver* S = new Solver();
   S->nx = nx; S->ny = ny; S->dim = ny > 1 ? 2 : 1; S->nv = S->dim + 2;
   S->order = order; S->recon = recon; S->bcx = bc_x; S->bcy = bc_y;

@@ -79,7 +79,7 @@ class State:
     x1: float
     y0: float = 0.0
     y1: float = 1.0
-    bc_x: int = 0          # 0 periodic, 1 transmissive
+    bc_x: int = 0          # 0 periodic, 1 transmissive, 2 reflecting wall
     bc_y: int = 0
     mu: float = 0.0
     Pr: float = 1.0
@@ -224,6 +224,19 @@ def acoustic_1d(N: int = 40, gamma: float = 1.4, order: int = 8, recon: int = 0)
                  t_end=0.01, name="acoustic_1d")
 
 
+def wall_impact_1d(N: int, u0: float = 0.5, rho: float = 1.0, p: float = 1.0,
+                   gamma: float = 1.4, order: int = 8, recon: int = 1) -> State:
+    """Uniform flow (rho, u0, p) in a tube [0, 1] closed by reflecting walls at both ends.
+    Until the waves from the two walls meet, the solution near x = 1 is the Riemann problem
+    of (rho, u0, p) against its mirror image (rho, -u0, p) (two shocks; the wall keeps the
+    middle state at rest), and near x = 0 the one of (rho, -u0, p) against (rho, u0, p)
+    (two rarefactions).  t_end = 0.2 keeps the two wave systems apart for u0 <= 1."""
+    W, Wx = cell_state_1d([(0.0, 1.0, lambda x: (np.full_like(x, rho), np.full_like(x, u0),
+                                                  np.full_like(x, p)))], N, 0.0, 1.0, gamma)
+    return State(W, Wx, None, N, 1, gamma, 0.0, 1.0, bc_x=2, order=order, recon=recon,
+                 t_end=0.2, name="wall_impact_1d", meta=dict(state=(rho, u0, p)))
+
+
 # ---------------------------------------------------------------------------
 # 2D
 # ---------------------------------------------------------------------------
@@ -275,6 +288,29 @@ def isentropic_vortex_2d(n: int, t: float = 0.0, gamma: float = 1.4, order: int 
                                0.0, 10.0 * ny / n, gamma)
     return State(W, Wx, Wy, n, ny, gamma, 0.0, 10.0, 0.0, 10.0 * ny / n, 0, 0, order=order,
                  recon=recon, t_end=10.0, name="isentropic_vortex_2d")
+
+
+def box_pulse_point(x, y, gamma=1.4):
+    """Smooth pressure and density pulse off the centre of [0, 1]^2 with a swirl and a
+    uniform drift, so that every wall sees a normal and a tangential velocity."""
+    r2 = (x - 0.35) ** 2 + (y - 0.6) ** 2
+    g = np.exp(-r2 / 0.02)
+    rho = 1.0 + 0.3 * g
+    p = 1.0 + 0.5 * g
+    u = 0.2 - 2.0 * (y - 0.6) * g
+    v = -0.1 + 2.0 * (x - 0.35) * g
+    return conservative_2d(rho, u, v, p, gamma)
+
+
+def box_pulse_2d(n: int, ny: int | None = None, gamma: float = 1.4, mu: float = 0.0,
+                 Pr: float = 1.0, order: int = 8, recon: int = 0, bc_x: int = 2,
+                 bc_y: int = 2) -> State:
+    """box_pulse_point on [0, 1] x [0, ny/n] (reflecting walls by default)."""
+    ny = n if ny is None else ny
+    W, Wx, Wy = _cell_state_2d(lambda x, y: box_pulse_point(x, y, gamma), n, ny, 0.0, 1.0,
+                               0.0, ny / n, gamma)
+    return State(W, Wx, Wy, n, ny, gamma, 0.0, 1.0, 0.0, ny / n, bc_x, bc_y, mu=mu, Pr=Pr,
+                 order=order, recon=recon, t_end=0.5, name="box_pulse_2d")
 
 
 def vortex_exact_avg(n: int, t: float, gamma: float = 1.4, ny: int | None = None) -> np.ndarray:
