@@ -38,26 +38,26 @@ def metric_of(args):
     return METRIC_SHEAR if args.workload == "shear" else METRIC
 UNIT = "cell-updates/s"
 CFL = 0.3
-# Per-unit figures of the kernels of a step (2D, 8th order, linear Euler), with their derivation
-# in DESIGN.md.  unit: "face" (sweeps) or "cell" (updates).  f32 / f64: floating-point operations
-# per unit (FMA = 2) from ncu's executed-instruction counters; bytes: algorithmic bytes per unit
-# (each datum read or written once), given for the updates, whose limit is memory or the FP64
-# pipe (the sweeps are compute-side: issue-bound, DRAM below 20 %); traffic: DRAM bytes (read +
-# write) per unit from one ncu capture of the 1024^2 case, scaled to a launch by the units
-# processed (the kernels stream, so traffic grows in proportion; at 1024^2 part of the data
-# stays in L2, so it reads low).
-# Sources: profiles/faces_2d_vortex_fp64.md, profiles/faces_2d_vortex_fp32bulk.md.
+# Per-unit figures of the kernels of a step (2D, 8th order, linear Euler).  unit: "face"
+# (sweeps) or "cell" (updates).  f32 / f64: floating-point operations per unit (FMA = 2) from
+# ncu's executed-instruction counters (FP32-bulk form: a 1024^2 capture; FP64 form: 256^2);
+# bytes: algorithmic bytes per unit (each datum read or written once), given for the updates,
+# whose limit is memory or the FP64 pipe (the sweeps are compute-side: issue-bound, DRAM below
+# 20 %); traffic: DRAM bytes (read + write) per unit from the 1024^2 capture, scaled to a launch
+# by the units processed (the kernels stream, so traffic grows in proportion; at 1024^2 part
+# of the data stays in L2, so it reads low).  The FP64 form has no traffic figure: its 256^2
+# capture fits in L2.
 KERNEL_MODEL = {
-    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1910.2},
-    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1910.2},
-    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1910.2},
-    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1910.2},
-    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2156.1, "f64": 35.0, "traffic": 158.0},
-    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2076.5, "f64": 35.0, "traffic": 161.5},
-    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 250.1},
+    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2},
+    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6},
+    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2},
+    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6},
+    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0},
+    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0},
+    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 249.0},
     ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0},
-    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.4},
-    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 345.1},
+    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0},
+    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 343.0},
 }
 HBM_FALLBACK_GBS = 6800.0
 
@@ -210,18 +210,52 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(st, dt, budget_s=12.0, window=128):
+def pinned_copy_gbs(n, reps=5):
+    """Host link bandwidth for one state: n float64 values copied between pinned host memory
+    and the device, each direction timed alone with CUDA events (the floor of the e2e step)."""
+    import torch
+    h = torch.empty(n, dtype=torch.float64).pin_memory()
+    d = torch.empty(n, dtype=torch.float64, device="cuda")
+    d.copy_(h, non_blocking=True)
+    h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    out = {}
+    for name, dst, src in (("h2d", d, h), ("d2h", h, d)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = reps * n * 8 / (a.elapsed_time(b) * 1e-3) / 1e9
+    del h, d
+    return out
+
+
+def window_state(st, w):
+    """The w x w window at the centre of the workload (through the vortex core, or across a
+    shear layer), as a problem of its own with transmissive edges."""
+    w = min(w, st.nx, st.ny)
+    i0, j0 = (st.nx - w) // 2, (st.ny - w) // 2
+    sl = (slice(None), slice(j0, j0 + w), slice(i0, i0 + w))
+    from paper_1901_00261_gb300 import inputs
+    return inputs.State(np.ascontiguousarray(st.W[sl]), np.ascontiguousarray(st.Wx[sl]),
+                        np.ascontiguousarray(st.Wy[sl]), w, w, st.gamma, 0.0, w * st.dx, 0.0,
+                        w * st.dy, 1, 1, mu=st.mu, Pr=st.Pr, order=st.order, recon=st.recon)
+
+
+def cpu_baseline(st, dt, budget_s=12.0, window=128, keep=None):
     """The oracle as it stands, on the host cores, on a window of the same workload
-    (transmissive window edges), as many steps as fit in the time budget."""
+    (transmissive window edges), as many steps as fit in the time budget.  keep (a dict):
+    receives the window problem, the step count and the oracle's final state."""
     import oracle
-    from paper_1901_00261_gb300 import inputs  # noqa: F401
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    w = min(window, st.nx)
-    sl = (slice(None), slice(0, w), slice(0, w))
-    O = oracle.Solver(w, w, st.gamma, st.mu, st.Pr, st.order, st.recon, 1, 1, 0.0, w * st.dx, 0.0, w * st.dy)
-    O.set_state(np.ascontiguousarray(st.W[sl]), np.ascontiguousarray(st.Wx[sl]),
-                np.ascontiguousarray(st.Wy[sl]))
+    ws = window_state(st, window)
+    w = ws.nx
+    O = oracle.Solver(w, w, ws.gamma, ws.mu, ws.Pr, ws.order, ws.recon, 1, 1, ws.x0, ws.x1, ws.y0, ws.y1)
+    O.set_state(ws.W, ws.Wx, ws.Wy)
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -231,8 +265,28 @@ def cpu_baseline(st, dt, budget_s=12.0, window=128):
         if el > budget_s or steps >= 50:
             break
     value = w * w * steps / el
+    if keep is not None:
+        keep.update(window=ws, steps=steps, state=O.get_state())
     return {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{w}x{w} window of the {st.nx}x{st.ny} workload, {steps} steps, {el:.1f} s"}
+            "sample": f"{w}x{w} window at the centre of the {st.nx}x{st.ny} workload, {steps} steps, {el:.1f} s"}
+
+
+def vs_oracle(keep, dt, forms):
+    """Both GPU forms on the oracle's window problem, same dt and step count: the L1 density
+    difference and the largest per-variable difference relative to max |W| (cell averages)."""
+    from paper_1901_00261_gb300 import gks
+    ws, steps, (Wo, _, _) = keep["window"], keep["steps"], keep["state"]
+    out = {"window": f"{ws.nx}x{ws.ny} centre, transmissive edges", "steps": steps}
+    for form in forms:
+        prec = gks.PREC_FP32_BULK if form == "fp32" else gks.PREC_FP64
+        G = gks.Solver.from_state(ws, precision=prec)
+        G.steps(dt, steps)
+        W = G.get_state()[0]
+        G.close()
+        out[form] = {"l1_rho": float(np.abs(W[0] - Wo[0]).mean()),
+                     "linf_rel": float(max(np.abs(W[v] - Wo[v]).max() / np.abs(Wo[v]).max()
+                                           for v in range(W.shape[0])))}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -433,6 +487,7 @@ def main():
             if args.workload == "vortex":
                 ex = inputs.vortex_exact_avg(args.n, T)
                 r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
+                r["linf_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).max())
             r["t_end"] = T
             results.setdefault("_W", {})[form] = W[0]
         results[form] = r
@@ -466,7 +521,8 @@ def main():
         el = time.perf_counter() - tw
         bytes_state = 3 * st.W.nbytes
         e2e = {"value": ncell * args.steps * ws / el, "unit": UNIT,
-               "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state}
+               "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
+               "copy_gbs": pinned_copy_gbs(st.W.size * 3)}
 
     if rank == 0:
         h = results[head]
@@ -480,13 +536,15 @@ def main():
                 "alu_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}}
         for form in forms:
             r = results[form]
-            line[form] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "l1_rho_vs_exact", "t_end",
-                                            "kernel_ms_per_launch") if k in r}
+            line[form] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "l1_rho_vs_exact",
+                                            "linf_rho_vs_exact", "t_end", "kernel_ms_per_launch") if k in r}
         if "_W" in results and len(results["_W"]) == 2:
             a, b = results["_W"]["fp32"], results["_W"]["fp64"]
             line["fp32_vs_fp64_l1_rho"] = float(np.abs(a - b).mean())
         if not args.no_cpu and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(st, dt)
+            keep = {}
+            line["cpu_baseline"] = cpu_baseline(st, dt, keep=keep)
+            line["vs_oracle"] = vs_oracle(keep, dt, forms)
         print(json.dumps(line), flush=True)
     for form in forms:
         results["_solver"][form][0].close()

@@ -44,7 +44,13 @@ typedef enum gks_status {
 } gks_status;
 
 enum { GKS_RECON_LINEAR = 0, GKS_RECON_WENOZ = 1 };
-enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1 };
+/* Boundary conditions per axis, applied through two ghost cells per side:
+ * GKS_BC_PERIODIC; GKS_BC_TRANSMISSIVE (ghosts copy the boundary cell's W and gradients);
+ * GKS_BC_REFLECTING, a solid wall (the reflecting boundary of the blast-wave and
+ * double-Mach tests of Sec. 5): ghost k outside the wall is the mirror image of cell k
+ * inside, with the momentum normal to the wall negated and, of the gradient normal to the
+ * wall, every component but that momentum's negated. */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_REFLECTING = 2 };
 /* GKS_PREC_FP64: every step in FP64.
  * GKS_PREC_FP32_BULK: reconstruction, WENO-Z and gas-kinetic arithmetic of the face sweeps in
  * FP32 on differences from a reference cell (the state mirrored as float hi/lo pairs); the
@@ -54,8 +60,7 @@ enum { GKS_PREC_FP64 = 0, GKS_PREC_FP32_BULK = 1 };
 
 typedef struct gks_opts {
   double x0, x1, y0, y1;   /* domain; dx = (x1 - x0)/nx, dy = (y1 - y0)/ny */
-  int bc_x, bc_y;          /* GKS_BC_PERIODIC or GKS_BC_TRANSMISSIVE (ghost cells copy the
-                              boundary cell's W and gradients) */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC, GKS_BC_TRANSMISSIVE or GKS_BC_REFLECTING */
   int precision;           /* GKS_PREC_FP64 or GKS_PREC_FP32_BULK */
   double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-12 */
   double eps_tau, C_tau;   /* numerical collision time eps*dt + C|pl-pr|/(pl+pr) dt of Sec. 4;
@@ -141,7 +146,8 @@ typedef struct gks_problem {
   int order, recon;        /* 6 | 8; GKS_RECON_LINEAR | GKS_RECON_WENOZ */
   double gamma, mu, Pr;    /* as in gks_create */
   double x0, x1, y0, y1;   /* domain */
-  int bc_x, bc_y;          /* GKS_BC_PERIODIC | GKS_BC_TRANSMISSIVE */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC | GKS_BC_TRANSMISSIVE (reflecting walls run
+                              in the single-problem solvers only) */
 } gks_problem;
 
 /* Create a batch of n problems (copied); device memory for all of them is one allocation.
@@ -198,7 +204,8 @@ void gks_batch_destroy(gks_batch* b);
  * status word it clears at its start: calls that overlap on the GPU (other streams or
  * threads) race.  Runs on `stream` (NULL: the legacy default stream) and synchronises it
  * before returning; returns GKS_OK, GKS_EINVAL, GKS_ECUDA or GKS_ENONPHYSICAL, with the
- * message in gks_static_last_error(). */
+ * message in gks_static_last_error().  bc: GKS_BC_PERIODIC, GKS_BC_TRANSMISSIVE or
+ * GKS_BC_REFLECTING at both ends. */
 #define GKS_STATIC_MAX_NX 16384
 int gks_step_1d_static(const double* W, const double* Wx, double* W_out, double* Wx_out,
                        int nx, double gamma, double mu, double Pr, double x0, double x1,

@@ -191,7 +191,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   gks_opts o;
   if (opts) o = *opts; else gks_default_opts(&o);
   if (!(o.x1 > o.x0) || (ny > 1 && !(o.y1 > o.y0))) { fail(GKS_EINVAL, "empty domain%s"); return nullptr; }
-  if ((o.bc_x != 0 && o.bc_x != 1) || (o.bc_y != 0 && o.bc_y != 1)) { fail(GKS_EINVAL, "bc must be 0 or 1%s"); return nullptr; }
+  if (o.bc_x < 0 || o.bc_x > 2 || o.bc_y < 0 || o.bc_y > 2) { fail(GKS_EINVAL, "bc must be 0, 1 or 2%s"); return nullptr; }
   if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_FP32_BULK) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
   if (o.tau_mode != 0 && o.tau_mode != 1) { fail(GKS_EINVAL, "tau_mode must be 0 or 1%s"); return nullptr; }

@@ -385,6 +385,8 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     if (q.order != 6 && q.order != 8) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": order must be 6 or 8"); delete B; return nullptr; }
     if (q.recon != 0 && q.recon != 1) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": recon must be 0 or 1"); delete B; return nullptr; }
     if (!(q.gamma > 1.0) || !(q.mu >= 0.0) || !(q.Pr > 0.0) || !(q.x1 > q.x0) || (q.ny > 1 && !(q.y1 > q.y0))) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": invalid physics or domain"); delete B; return nullptr; }
+    // reflecting walls run in the single-problem solvers only (the persistent kernel is
+    // compiled without the wall signs)
     if ((q.bc_x != 0 && q.bc_x != 1) || (q.bc_y != 0 && q.bc_y != 1)) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": bc must be 0 or 1"); delete B; return nullptr; }
     const int dim = q.ny > 1 ? 2 : 1, N = dim + 2;
     if (dim == 2 && (q.recon == 1 || q.mu > 0.0)) B->cls = 1;

@@ -62,11 +62,12 @@ __global__ void __launch_bounds__(128) faces_1d_kernel(FaceArgs a) {
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     int c = map_index(f - 2 + o, a.nx, a.bcx);
+    R w[N], g[N];
 #pragma unroll
-    for (int v = 0; v < N; ++v) {
-      in[v][o] = a.W[v * ncell + c];
-      in[v][4 + o] = a.dn * a.Wn[v * ncell + c];
-    }
+    for (int v = 0; v < N; ++v) { w[v] = a.W[v * ncell + c]; g[v] = a.Wn[v * ncell + c]; }
+    if (a.bcx == 2) mirror_ghost<1, 0, R>(w, nullptr, g, beyond_wall(f - 2 + o, a.nx, 2), false);
+#pragma unroll
+    for (int v = 0; v < N; ++v) { in[v][o] = w[v]; in[v][4 + o] = a.dn * g[v]; }
   }
   R rec[WENO ? 7 : 3][N];
   normal_recon<R, 1, ORDER, WENO>(in, R(a.dn), R(a.P.gamma), R(a.P.weno_eps), rec, nullptr);
@@ -117,11 +118,17 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   const int nn = DIR == 0 ? a.nx + 1 : a.ny + 1;
 
   // ---- phase 1: normal reconstruction of every face of the tile plus tangential halo ----
+  // reflecting walls on either axis (uniform over the grid: periodic and transmissive
+  // grids skip the mirror signs)
+  const int bcn = DIR == 0 ? a.bcx : a.bcy, bct = DIR == 0 ? a.bcy : a.bcx;
+  const bool walls = (bcn == 2) | (bct == 2);
   for (int s = tid; s < T::NS; s += nthreads) {
     int sa = s % T::SA, sb = s / T::SA;
-    int fn, ct;   // normal face index, tangential cell index
-    if (DIR == 0) { fn = blockIdx.x * TA + sa; ct = map_index(blockIdx.y * TB + sb - 2, a.ny, a.bcy); }
-    else { ct = map_index(blockIdx.x * TA + sa - 2, a.nx, a.bcx); fn = blockIdx.y * TB + sb; }
+    int fn, ctr;   // normal face index, tangential cell index (before mapping)
+    if (DIR == 0) { fn = blockIdx.x * TA + sa; ctr = blockIdx.y * TB + sb - 2; }
+    else { ctr = blockIdx.x * TA + sa - 2; fn = blockIdx.y * TB + sb; }
+    const int ct = DIR == 0 ? map_index(ctr, a.ny, a.bcy) : map_index(ctr, a.nx, a.bcx);
+    const int nnc = DIR == 0 ? a.nx : a.ny, ntc = DIR == 0 ? a.ny : a.nx;
     R rec[NQ][N];
     if (fn < nn) {
       R in[N][8];
@@ -133,6 +140,9 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
         double w[N], g[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) { w[v] = a.W[v * ncell + c]; g[v] = a.Wn[v * ncell + c]; }
+        if (walls)
+          mirror_ghost<2, DIR, double>(w, nullptr, g, beyond_wall(fn - 2 + o, nnc, bcn),
+                                       beyond_wall(ctr, ntc, bct));
         if (DIR == 1) { swap_uv<2>(w); swap_uv<2>(g); }
 #pragma unroll
         for (int v = 0; v < N; ++v) { in[v][o] = w[v]; in[v][4 + o] = a.dn * g[v]; }

@@ -14,12 +14,19 @@ cudaError_t launch_mirror(const double* S, float* M, int nx, int ny, int dim, cu
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Grids with a reflecting wall run the instantiations compiled with the wall signs.
 template <int ORDER, bool WENO, bool VISC>
 static cudaError_t launch_1d32_t(const FaceArgs32& a, cudaStream_t s) {
   int threads = 128;
   int blocks = (a.nx + 1 + threads - 1) / threads;
-  if (a.stage == 1) faces_1d_f32_kernel<ORDER, WENO, VISC, 1><<<blocks, threads, 0, s>>>(a);
-  else faces_1d_f32_kernel<ORDER, WENO, VISC, 2><<<blocks, threads, 0, s>>>(a);
+  const bool walls = a.bcx == 2;
+  if (a.stage == 1) {
+    if (walls) faces_1d_f32_kernel<ORDER, WENO, VISC, 1, true><<<blocks, threads, 0, s>>>(a);
+    else faces_1d_f32_kernel<ORDER, WENO, VISC, 1, false><<<blocks, threads, 0, s>>>(a);
+  } else {
+    if (walls) faces_1d_f32_kernel<ORDER, WENO, VISC, 2, true><<<blocks, threads, 0, s>>>(a);
+    else faces_1d_f32_kernel<ORDER, WENO, VISC, 2, false><<<blocks, threads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -37,17 +44,17 @@ cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool vi
 #define SWEEP32_FPT 2
 #endif
 
-template <int ORDER, bool WENO, bool VISC, int DIR>
+template <int ORDER, bool WENO, bool VISC, int DIR, bool WALLS>
 static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   const int FPT = SWEEP32_FPT;
   typedef Tile32<DIR, FPT> T;
   const size_t shmem = T::smem_bytes(WENO);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1>,
+    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2>,
+      e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -56,14 +63,17 @@ static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + 1 + TA32 - 1) / TA32, (a.ny + T::TB - 1) / T::TB);
   else grid = dim3((a.nx + TA32 - 1) / TA32, (a.ny + 1 + T::TB - 1) / T::TB);
-  if (a.stage == 1) faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1><<<grid, block, shmem, s>>>(a);
-  else faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2><<<grid, block, shmem, s>>>(a);
+  if (a.stage == 1) faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS><<<grid, block, shmem, s>>>(a);
+  else faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int ORDER, bool WENO, bool VISC>
 static cudaError_t launch_2d32_dir(const FaceArgs32& a, int dir, cudaStream_t s) {
-  return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0>(a, s) : launch_2d32_t<ORDER, WENO, VISC, 1>(a, s);
+  const bool walls = a.bcx == 2 || a.bcy == 2;
+  if (walls)
+    return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, true>(a, s) : launch_2d32_t<ORDER, WENO, VISC, 1, true>(a, s);
+  return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, false>(a, s) : launch_2d32_t<ORDER, WENO, VISC, 1, false>(a, s);
 }
 
 cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon, bool visc, cudaStream_t s) {

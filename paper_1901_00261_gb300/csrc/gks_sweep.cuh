@@ -5,6 +5,12 @@
 
 namespace gks {
 
+// Cell holding the data of index i of a line of n cells.  bc 0 periodic; bc 1 transmissive
+// (the boundary cell); bc 2 reflecting wall: the mirror image across the wall (index -1 is
+// cell 0, index n is cell n - 1), whose signs mirror_ghost applies.  Indices further out
+// than n, which only the overhang of a tile beyond the grid reaches and no face uses, are
+// clamped into the grid.  WALLS = false: a kernel launched only for bc 0 and 1.
+template <bool WALLS = true>
 __device__ __forceinline__ int map_index(int i, int n, int bc) {
   if (bc == 0) {
     // indices lie within a few cells of [0, n): one add or subtract; the remainder only for
@@ -13,7 +19,38 @@ __device__ __forceinline__ int map_index(int i, int n, int bc) {
     else if (i < 0) { i += n; if (i < 0) { i %= n; if (i < 0) i += n; } }
     return i;
   }
+  if (WALLS && bc == 2) { if (i < 0) i = -1 - i; else if (i >= n) i = 2 * n - 1 - i; }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// True when index i of a line of n cells lies beyond a reflecting wall.
+__device__ __forceinline__ bool beyond_wall(int i, int n, int bc) {
+  return bc == 2 && (unsigned)i >= (unsigned)n;
+}
+
+// Mirror image of a cell beyond a reflecting wall (conservative variables in the global
+// frame).  rn: the wall is crossed by the stencil direction DIR (its normal momentum
+// 1 + DIR changes sign, and so do the derivatives along DIR of the other variables);
+// rt (2D): the wall is crossed along the tangential axis (the momentum 2 - DIR changes
+// sign, in the value and in its derivative along DIR).  w: values (and wlo, the low parts
+// of a hi/lo pair, or nullptr); g: derivatives along DIR (or nullptr).
+template <int DIM, int DIR, typename R>
+__device__ __forceinline__ void mirror_ghost(R* w, R* wlo, R* g, bool rn, bool rt) {
+  const int N = DIM + 2, an = 1 + DIR, at = 2 - DIR;
+  if (rn) {
+    w[an] = -w[an];
+    if (wlo) wlo[an] = -wlo[an];
+    if (g) {
+#pragma unroll
+      for (int v = 0; v < N; ++v)
+        if (v != an) g[v] = -g[v];
+    }
+  }
+  if (DIM == 2 && rt) {
+    w[at] = -w[at];
+    if (wlo) wlo[at] = -wlo[at];
+    if (g) g[at] = -g[at];
+  }
 }
 
 // Tangential quartic through the averages over the five unit segments centred at -2..2:

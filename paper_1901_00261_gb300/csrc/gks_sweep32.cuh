@@ -125,10 +125,13 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
 // precision: across cell i its difference is A_{i+1/2} + D_{i-1/2}.  F, Ft, dW0, Wt, Wtt,
 // dFc in the global frame; cl, cr: the face's left and right cells.
 // STAGE: 1 or 2 fixed at compile time, 0 read from a.stage.
+// ml, mr: the left / right cell lies beyond a reflecting wall (its state is the mirror image
+// of cell cl / cr, with the momentum normal to the face negated).
 template <int DIM, int DIR, bool CG, int STAGE = 0>
 __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, long nfaces, long cl, long cr,
                                              const float* F, const float* Ft, const float* dW0,
-                                             const float* Wt, const float* Wtt, const float* dFc) {
+                                             const float* Wt, const float* Wtt, const float* dFc,
+                                             bool ml = false, bool mr = false) {
   const int N = DIM + 2;
   const long ncell = (long)a.nx * a.ny;
   double* o64 = static_cast<double*>(a.out);
@@ -150,6 +153,8 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
     double wl[N], wr[N], Fref[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) { wl[v] = ldd<CG>(a.W + v * ncell + cl); wr[v] = ldd<CG>(a.W + v * ncell + cr); }
+    if (ml) wl[1 + DIR] = -wl[1 + DIR];
+    if (mr) wr[1 + DIR] = -wr[1 + DIR];
     euler_flux64<DIM, DIR>(wl, a.P.gamma, Fref);
     const double dt = ldd<CG>(&tc->dt);
 #pragma unroll
@@ -173,27 +178,37 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
 // 1D FP32-bulk sweep: one thread per face f = 0..nx.
 // ---------------------------------------------------------------------------
 // STAGE: 1 or 2 fixed at compile time (stage 2 needs only F_t and W_tt), 0 read from a.stage.
-template <int ORDER, bool WENO, bool VISC, bool CG, int STAGE = 0>
+// WALLS: compiled with the reflecting-wall signs (launched for bc 2 only; the periodic and
+// transmissive launches carry none of that code).
+template <int ORDER, bool WENO, bool VISC, bool CG, int STAGE = 0, bool WALLS = false>
 __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
   const int N = 3;
   if (f > a.nx) return;
   const int stage = STAGE ? STAGE : a.stage;
-  prefetch_face_epilogue<1, CG>(a, stage, f, a.nx + 1, map_index(f - 1, a.nx, a.bcx), map_index(f, a.nx, a.bcx));
+  prefetch_face_epilogue<1, CG>(a, stage, f, a.nx + 1, map_index<WALLS>(f - 1, a.nx, a.bcx), map_index<WALLS>(f, a.nx, a.bcx));
   const double dt = ldd<CG>(a.dtp);
   const long ncell = a.nx;
   const long L = N * ncell;
   float in[N][8], ref[N];
-  int cref = map_index(f - 1, a.nx, a.bcx);
+  int cref = map_index<WALLS>(f - 1, a.nx, a.bcx);
+  const bool walls = WALLS && a.bcx == 2;
   float rlo[N];
 #pragma unroll
   for (int v = 0; v < N; ++v) { ref[v] = ldf<CG>(a.M + v * ncell + cref); rlo[v] = ldf<CG>(a.M + L + v * ncell + cref); }
+  if (walls) mirror_ghost<1, 0, float>(ref, rlo, nullptr, beyond_wall(f - 1, a.nx, 2), false);
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
-    int c = map_index(f - 2 + o, a.nx, a.bcx);
+    int c = map_index<WALLS>(f - 2 + o, a.nx, a.bcx);
+    float hi[N], lo[N], g[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      in[v][o] = (ldf<CG>(a.M + v * ncell + c) - ref[v]) + (ldf<CG>(a.M + L + v * ncell + c) - rlo[v]);
-      in[v][4 + o] = a.dnf * ldf<CG>(a.Mn + v * ncell + c);
+      hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); g[v] = ldf<CG>(a.Mn + v * ncell + c);
+    }
+    if (walls) mirror_ghost<1, 0, float>(hi, lo, g, beyond_wall(f - 2 + o, a.nx, 2), false);
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      in[v][o] = (hi[v] - ref[v]) + (lo[v] - rlo[v]);
+      in[v][4 + o] = a.dnf * g[v];
     }
   }
   float rec[WENO ? 7 : 3][N];
@@ -217,12 +232,13 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
   float dFc[N] = {0.f, 0.f, 0.f};
   if (stage == 1) euler_flux_delta<float, 1>(ref, dr, a.gammaf, dFc);
-  write_face32<1, 0, CG, STAGE>(a, f, a.nx + 1, cref, map_index(f, a.nx, a.bcx), po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc);
+  write_face32<1, 0, CG, STAGE>(a, f, a.nx + 1, cref, map_index<WALLS>(f, a.nx, a.bcx), po.F, po.Ft, po.W0, po.Wt, po.Wtt, dFc,
+                                walls && f == 0, walls && f == a.nx);
 }
 
-template <int ORDER, bool WENO, bool VISC, int STAGE>
+template <int ORDER, bool WENO, bool VISC, int STAGE, bool WALLS>
 __global__ void __launch_bounds__(128) faces_1d_f32_kernel(FaceArgs32 a) {
-  sweep1d_f32_face<ORDER, WENO, VISC, false, STAGE>(a, blockIdx.x * blockDim.x + threadIdx.x);
+  sweep1d_f32_face<ORDER, WENO, VISC, false, STAGE, WALLS>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,7 +264,8 @@ struct Tile32 {
 // One tile of TA32 x TB32 faces; tid = linear thread index in a block of TA32 * TB32 threads;
 // (bx, by) = tile coordinates (the block indices of the standalone launch); smf = dynamic
 // shared memory of (NQ + 2) * 4 * NS floats.
-template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1, int STAGE = 0>
+// WALLS: as for sweep1d_f32_face.
+template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1, int STAGE = 0, bool WALLS = false>
 __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, int by, int tid, float* smf) {
   const int stage = STAGE ? STAGE : a.stage;
   const int N = 4;
@@ -264,31 +281,39 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   const int nthreads = TA32 * TB32;
   const int nn = DIR == 0 ? a.nx + 1 : a.ny + 1;
 
+  // reflecting walls on either axis
+  const int bcn = DIR == 0 ? a.bcx : a.bcy, bct = DIR == 0 ? a.bcy : a.bcx;
+  const int nnc = DIR == 0 ? a.nx : a.ny, ntc = DIR == 0 ? a.ny : a.nx;
+  const bool walls = WALLS && ((bcn == 2) | (bct == 2));
   for (int s = tid; s < T::NS; s += nthreads) {
     int sa = s % T::SA, sb = s / T::SA;
-    int fn, ct;
-    if (DIR == 0) { fn = bx * TA32 + sa; ct = map_index(by * T::TB + sb - 2, a.ny, a.bcy); }
-    else { ct = map_index(bx * TA32 + sa - 2, a.nx, a.bcx); fn = by * T::TB + sb; }
+    int fn, ctr;   // normal face index, tangential cell index (before mapping)
+    if (DIR == 0) { fn = bx * TA32 + sa; ctr = by * T::TB + sb - 2; }
+    else { ctr = bx * TA32 + sa - 2; fn = by * T::TB + sb; }
+    const int ct = DIR == 0 ? map_index<WALLS>(ctr, a.ny, a.bcy) : map_index<WALLS>(ctr, a.nx, a.bcx);
     float rec[NQ][N];
     float ref[N], rlo[N], dfc[N] = {0.f, 0.f, 0.f, 0.f};
     if (fn < nn) {
+      const bool rt = walls && beyond_wall(ctr, ntc, bct);
       long cr;
-      if (DIR == 0) cr = (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx);
-      else cr = (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
+      if (DIR == 0) cr = (long)ct * a.nx + map_index<WALLS>(fn - 1, a.nx, a.bcx);
+      else cr = (long)map_index<WALLS>(fn - 1, a.ny, a.bcy) * a.nx + ct;
 #pragma unroll
       for (int v = 0; v < N; ++v) { ref[v] = ldf<CG>(a.M + v * ncell + cr); rlo[v] = ldf<CG>(a.M + L + v * ncell + cr); }
+      if (walls) mirror_ghost<2, DIR, float>(ref, rlo, nullptr, beyond_wall(fn - 1, nnc, bcn), rt);
       if (DIR == 1) { swap_uv_f<2>(ref); swap_uv_f<2>(rlo); }
       float in[N][8];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         long c;
-        if (DIR == 0) c = (long)ct * a.nx + map_index(fn - 2 + o, a.nx, a.bcx);
-        else c = (long)map_index(fn - 2 + o, a.ny, a.bcy) * a.nx + ct;
+        if (DIR == 0) c = (long)ct * a.nx + map_index<WALLS>(fn - 2 + o, a.nx, a.bcx);
+        else c = (long)map_index<WALLS>(fn - 2 + o, a.ny, a.bcy) * a.nx + ct;
         float hi[N], lo[N], g[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
           hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); g[v] = ldf<CG>(a.Mn + v * ncell + c);
         }
+        if (walls) mirror_ghost<2, DIR, float>(hi, lo, g, beyond_wall(fn - 2 + o, nnc, bcn), rt);
         if (DIR == 1) { swap_uv_f<2>(hi); swap_uv_f<2>(lo); swap_uv_f<2>(g); }
 #pragma unroll
         for (int v = 0; v < N; ++v) {
@@ -334,10 +359,10 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   {
     const long pf = DIR == 0 ? (long)ct * (a.nx + 1) + fn : (long)fn * a.nx + ct;
     const long pn = DIR == 0 ? (long)a.ny * (a.nx + 1) : (long)(a.ny + 1) * a.nx;
-    const long pl = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
-                             : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
-    const long pr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
-                             : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
+    const long pl = DIR == 0 ? (long)ct * a.nx + map_index<WALLS>(fn - 1, a.nx, a.bcx)
+                             : (long)map_index<WALLS>(fn - 1, a.ny, a.bcy) * a.nx + ct;
+    const long pr = DIR == 0 ? (long)ct * a.nx + map_index<WALLS>(fn, a.nx, a.bcx)
+                             : (long)map_index<WALLS>(fn, a.ny, a.bcy) * a.nx + ct;
     prefetch_face_epilogue<2, CG>(a, stage, pf, pn, pl, pr);
   }
   int slot[5];
@@ -415,22 +440,23 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   if (DIR == 0) { face = (long)ct * (a.nx + 1) + fn; nfaces = (long)a.ny * (a.nx + 1); }
   else { face = (long)fn * a.nx + ct; nfaces = (long)(a.ny + 1) * a.nx; }
   // the face's left (reference) and right cells
-  const long cl = DIR == 0 ? (long)ct * a.nx + map_index(fn - 1, a.nx, a.bcx)
-                           : (long)map_index(fn - 1, a.ny, a.bcy) * a.nx + ct;
-  const long cr = DIR == 0 ? (long)ct * a.nx + map_index(fn, a.nx, a.bcx)
-                           : (long)map_index(fn, a.ny, a.bcy) * a.nx + ct;
-  write_face32<2, DIR, CG, STAGE>(a, face, nfaces, cl, cr, F, Ft, dW0, Wt, Wtt, dFc);
+  const long cl = DIR == 0 ? (long)ct * a.nx + map_index<WALLS>(fn - 1, a.nx, a.bcx)
+                           : (long)map_index<WALLS>(fn - 1, a.ny, a.bcy) * a.nx + ct;
+  const long cr = DIR == 0 ? (long)ct * a.nx + map_index<WALLS>(fn, a.nx, a.bcx)
+                           : (long)map_index<WALLS>(fn, a.ny, a.bcy) * a.nx + ct;
+  write_face32<2, DIR, CG, STAGE>(a, face, nfaces, cl, cr, F, Ft, dW0, Wt, Wtt, dFc,
+                                  walls && beyond_wall(fn - 1, nnc, bcn), walls && beyond_wall(fn, nnc, bcn));
   }
 }
 
 // Linear Euler tiles: five blocks (20 warps) per SM, measured fastest for both stages (the
 // first stage spills a few bytes at that bound); the WENO-Z / viscous tiles are left to the
 // compiler.
-template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE, bool WALLS>
 __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 5)
 faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE, WALLS>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,7 +17,7 @@ from . import build as _build
 GKS_OK, GKS_EINVAL, GKS_ECUDA, GKS_ENOMEM, GKS_ENONPHYSICAL, GKS_ETIMEOUT = 0, -1, -2, -3, -4, -5
 RECON_LINEAR, RECON_WENOZ = 0, 1
 PREC_FP64, PREC_FP32_BULK = 0, 1
-BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None

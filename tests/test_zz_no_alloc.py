@@ -27,14 +27,19 @@ def test_header_limit_matches_binding():
     assert m and int(m.group(1)) == gks.STATIC_MAX_NX
 
 
-@pytest.mark.parametrize("order,recon,N", [(6, 0, 80), (8, 1, 1000)])
-def test_static_step_matches_allocating_entry_point(order, recon, N):
+@pytest.mark.parametrize("order,recon,N,wall", [(6, 0, 80, False), (8, 1, 1000, False),
+                                                (8, 1, 400, True)])
+def test_static_step_matches_allocating_entry_point(order, recon, N, wall):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     L = gks.lib()
-    st = inputs.density_wave_1d(N, order=order, recon=recon) if recon == 0 else \
-        inputs.sod_1d(N, order=order, recon=recon)
+    if wall:
+        st = inputs.wall_impact_1d(N, order=order, recon=recon)
+    elif recon == 0:
+        st = inputs.density_wave_1d(N, order=order, recon=recon)
+    else:
+        st = inputs.sod_1d(N, order=order, recon=recon)
     ref = gks.Solver.from_state(st)
     dt = 0.3 / ref.max_wavespeed()
 
