@@ -108,7 +108,25 @@ int gks_steps(gks_ctx* ctx, double dt, int nsteps);
 /* max over cells of (|U| + c)/dx (+ (|V| + c)/dy in 2D); dt = CFL / *out.  Synchronises. */
 int gks_max_wavespeed(gks_ctx* ctx, double* out);
 
-/* Wait for the context stream; report device conditions. */
+/* Pipelined step from host memory to host memory, for a stream of independent steps (an
+ * ensemble of states, each advanced by one step): copies W, Wx (, Wy) from host memory into
+ * one of three device slots, advances that copy one two-stage step of size dt > 0 with the
+ * context's scheme, and copies the result into W_out, Wx_out (, Wy_out) in host memory
+ * (layout as gks_set_state; Wy and Wy_out NULL in 1D).  Returns without waiting: the copy-in
+ * of one call, the step of the call before and the copy-out of the call before that run at
+ * the same time (two copy streams beside the context stream), so a run of calls costs about
+ * the slowest of the three per call rather than their sum.  The steps run in order with the
+ * context's other work; the context's own state is not read or changed.  Every host buffer
+ * must stay valid, and the outputs unread, until gks_sync returns; outputs of calls that may
+ * be in flight together must not overlap.  Pinned host memory (cudaHostAlloc,
+ * cudaHostRegister) gives the overlap; pageable memory works but the copies serialise.  The
+ * first call allocates the three slots (three times the state).  Returns GKS_OK,
+ * GKS_EINVAL, GKS_ENOMEM or GKS_ECUDA; non-physical states are reported by gks_sync. */
+int gks_step_host_async(gks_ctx* ctx, const double* W, const double* Wx, const double* Wy,
+                        double* W_out, double* Wx_out, double* Wy_out, double dt);
+
+/* Wait for the context stream and any gks_step_host_async copies; report device
+ * conditions. */
 int gks_sync(gks_ctx* ctx);
 
 /* Device addresses of the state arrays held by the context (valid until gks_destroy). */

@@ -50,6 +50,21 @@ struct gks_ctx {
   double last_dt = -1.0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // FP32-bulk: the float mirror holds a pipeline slot's state, not `state` (rebuilt before the
+  // next step of the context's own state)
+  bool mirror_foreign = false;
+  // pipelined host-to-host steps (gks_step_host_async): three state slots and three streams
+  // of its own (copy-in, step, copy-out; created together so that they do not share a
+  // hardware queue with one another, where they would run in submission order);
+  // ev_in / ev_done / ev_out mark a slot's copy-in, step and copy-out.  pipe_pending: a
+  // pipelined step may still be running, which the context stream joins (ev_done[pipe_last])
+  // before its own next use of the shared buffers.
+  double* slots = nullptr;
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[3] = {}, ev_done[3] = {}, ev_out[3] = {}, ev_ctx = nullptr;
+  long pipe_calls = 0;
+  int pipe_last = 0;
+  bool pipe_pending = false;
 };
 
 namespace {
@@ -58,7 +73,9 @@ long state_len(const gks_ctx* c) { return (long)c->nv * c->ncell; }
 
 // Enqueue the two-stage step (no dt update) on the context stream.  When ev is given,
 // launch slot k is bracketed by events ev[2k], ev[2k+1].
-int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
+// state: the state to advance (default: the context's own).
+int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr, double* state = nullptr) {
+  double* const S = state ? state : c->state;
   int slot = 0;
   auto mark = [&](bool begin) {
     if (ev) cudaEventRecord(ev[2 * slot + (begin ? 0 : 1)], c->stream);
@@ -73,12 +90,12 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
     fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
     fa.P = c->P;
     fa.M = c->mirror;
-    fa.W = c->state;
+    fa.W = S;
     fa.dnf = (float)c->dx; fa.gammaf = (float)c->P.gamma; fa.epsf = (float)c->P.weno_eps;
     const bool visc = c->P.mu > 0.0 || c->P.tau_mode == 1;
     gks::UpdateArgs32 ua;
     ua.fx = reinterpret_cast<float*>(c->fx); ua.fy = reinterpret_cast<float*>(c->fy);
-    ua.W = c->state; ua.M = c->mirror;
+    ua.W = S; ua.M = c->mirror;
     ua.nx = c->nx; ua.ny = c->ny; ua.bcx = c->o.bc_x; ua.bcy = c->o.bc_y;
     ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy;
     for (int stage = 1; stage <= 2; ++stage) {
@@ -115,7 +132,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
   ua.fx = c->fx; ua.fy = c->fy; ua.acc = c->acc;
   ua.nx = c->nx; ua.ny = c->ny; ua.idx = 1.0 / c->dx; ua.idy = 1.0 / c->dy;
   for (int stage = 1; stage <= 2; ++stage) {
-    const double* W = stage == 1 ? c->state : c->stage;
+    const double* W = stage == 1 ? S : c->stage;
     fa.stage = stage;
     fa.W = W;
     // x faces
@@ -133,7 +150,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
       if (e != cudaSuccess) return cuda_fail(e, "y-face sweep");
     }
     ua.W = W;
-    ua.Ws = stage == 1 ? c->stage : c->state;
+    ua.Ws = stage == 1 ? c->stage : S;
     mark(true);
     e = gks::launch_update(ua, c->dim, stage, c->stream);
     mark(false);
@@ -142,15 +159,32 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr) {
   return GKS_OK;
 }
 
-// FP32-bulk: rebuild the float mirror after the FP64 state was replaced.
-int refresh_mirror(gks_ctx* c) {
+// FP32-bulk: rebuild the float mirror after the FP64 state was replaced (state: a pipeline
+// slot instead of the context's own state).
+int refresh_mirror(gks_ctx* c, double* state = nullptr) {
   if (c->o.precision != GKS_PREC_FP32_BULK) return GKS_OK;
-  cudaError_t e = gks::launch_mirror(c->state, c->mirror, c->nx, c->ny, c->dim, c->stream);
+  cudaError_t e = gks::launch_mirror(state ? state : c->state, c->mirror, c->nx, c->ny, c->dim, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mirror");
+  c->mirror_foreign = state != nullptr;
+  return GKS_OK;
+}
+
+// Before a step of the context's own state: the mirror must be that state's.
+int own_mirror(gks_ctx* c) { return c->mirror_foreign ? refresh_mirror(c) : GKS_OK; }
+
+// Order the context stream after the last pipelined step (they share the mirror, the face
+// buffers and the step constants).
+int join_pipeline(gks_ctx* c) {
+  if (!c->pipe_pending) return GKS_OK;
+  cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_done[c->pipe_last], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline join");
+  c->pipe_pending = false;
   return GKS_OK;
 }
 
 int check_status(gks_ctx* c) {
+  int jrc = join_pipeline(c);
+  if (jrc != GKS_OK) return jrc;
   unsigned int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -247,6 +281,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
 
 int gks_set_state(gks_ctx* c, const double* W, const double* Wx, const double* Wy) {
   if (!c || !W || !Wx || (c->dim == 2 && !Wy)) return fail(GKS_EINVAL, "NULL argument%s");
+  if (int jrc = join_pipeline(c)) return jrc;
   const long L = state_len(c);
   const double* src[3] = {W, Wx, Wy};
   for (int k = 0; k <= c->dim; ++k) {
@@ -262,6 +297,7 @@ int gks_set_state(gks_ctx* c, const double* W, const double* Wx, const double* W
 
 int gks_set_state_device(gks_ctx* c, const double* W, const double* Wx, const double* Wy) {
   if (!c || !W || !Wx || (c->dim == 2 && !Wy)) return fail(GKS_EINVAL, "NULL argument%s");
+  if (int jrc = join_pipeline(c)) return jrc;
   const long L = state_len(c);
   const double* src[3] = {W, Wx, Wy};
   for (int k = 0; k <= c->dim; ++k) {
@@ -273,6 +309,7 @@ int gks_set_state_device(gks_ctx* c, const double* W, const double* Wx, const do
 
 int gks_get_state(gks_ctx* c, double* W, double* Wx, double* Wy) {
   if (!c || !W || !Wx || (c->dim == 2 && !Wy)) return fail(GKS_EINVAL, "NULL argument%s");
+  if (int jrc = join_pipeline(c)) return jrc;
   const long L = state_len(c);
   double* dst[3] = {W, Wx, Wy};
   for (int k = 0; k <= c->dim; ++k) {
@@ -284,6 +321,7 @@ int gks_get_state(gks_ctx* c, double* W, double* Wx, double* Wy) {
 
 int gks_get_state_device(gks_ctx* c, double* W, double* Wx, double* Wy) {
   if (!c || !W || !Wx || (c->dim == 2 && !Wy)) return fail(GKS_EINVAL, "NULL argument%s");
+  if (int jrc = join_pipeline(c)) return jrc;
   const long L = state_len(c);
   double* dst[3] = {W, Wx, Wy};
   for (int k = 0; k <= c->dim; ++k) {
@@ -298,6 +336,9 @@ int gks_steps(gks_ctx* c, double dt, int nsteps) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(GKS_EINVAL, "dt must be finite and > 0%s");
   if (nsteps < 0) return fail(GKS_EINVAL, "nsteps must be >= 0%s");
   if (nsteps == 0) return GKS_OK;
+  if (int jrc = join_pipeline(c)) return jrc;
+  int mrc = own_mirror(c);
+  if (mrc != GKS_OK) return mrc;
   cudaError_t e;
   if (dt != c->last_dt) {
     e = gks::launch_set_times(reinterpret_cast<gks::StepTimes*>(c->d_dt), dt, c->stream);
@@ -338,6 +379,9 @@ int gks_steps_timed(gks_ctx* c, double dt, int nsteps, double* kernel_ms) {
   if (nsteps < 0) return fail(GKS_EINVAL, "nsteps must be >= 0%s");
   const int nl = gks_launches_per_step(c);
   for (int k = 0; k < nl; ++k) kernel_ms[k] = 0.0;
+  if (int jrc = join_pipeline(c)) return jrc;
+  int mrc = own_mirror(c);
+  if (mrc != GKS_OK) return mrc;
   cudaError_t e;
   if (dt != c->last_dt) {
     e = gks::launch_set_times(reinterpret_cast<gks::StepTimes*>(c->d_dt), dt, c->stream);
@@ -384,8 +428,79 @@ int gks_max_wavespeed(gks_ctx* c, double* out) {
   return check_status(c);
 }
 
+int gks_step_host_async(gks_ctx* c, const double* W, const double* Wx, const double* Wy,
+                        double* W_out, double* Wx_out, double* Wy_out, double dt) {
+  if (!c || !W || !Wx || !W_out || !Wx_out || (c->dim == 2 && (!Wy || !Wy_out)))
+    return fail(GKS_EINVAL, "NULL argument%s");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(GKS_EINVAL, "dt must be finite and > 0%s");
+  const long L = state_len(c);
+  const int narr = c->dim + 1;
+  const size_t bytes = (size_t)L * sizeof(double);
+  cudaError_t e;
+  if (!c->slots) {
+    e = cudaMalloc(&c->slots, 3 * (size_t)narr * bytes);
+    if (e != cudaSuccess) { c->slots = nullptr; return cuda_fail(e, "pipeline slots"); }
+    e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ctx, cudaEventDisableTiming);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[k], c->s_out);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline streams");
+  }
+  const int k = (int)(c->pipe_calls % 3);
+  double* slot = c->slots + (size_t)k * narr * L;
+  const double* src[3] = {W, Wx, Wy};
+  double* dst[3] = {W_out, Wx_out, Wy_out};
+  // copy-in once the slot's previous copy-out (three calls ago) has finished
+  e = cudaStreamWaitEvent(c->s_in, c->ev_out[k], 0);
+  for (int a = 0; a < narr && e == cudaSuccess; ++a)
+    e = cudaMemcpyAsync(slot + a * L, src[a], bytes, cudaMemcpyHostToDevice, c->s_in);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[k], c->s_in);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline copy-in");
+  // the step on the pipeline's own stream, after the context's earlier work (which may have
+  // replaced the mirror or the step constants) and after the slot's copy-in
+  e = cudaEventRecord(c->ev_ctx, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_comp, c->ev_ctx, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_comp, c->ev_in[k], 0);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline wait");
+  cudaStream_t own = c->stream;
+  c->stream = c->s_comp;   // the step's launches go to the pipeline stream
+  int rc = GKS_OK;
+  if (dt != c->last_dt) {
+    e = gks::launch_set_times(reinterpret_cast<gks::StepTimes*>(c->d_dt), dt, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dt update");
+    else c->last_dt = dt;
+  }
+  if (rc == GKS_OK) rc = refresh_mirror(c, slot);
+  if (rc == GKS_OK) rc = enqueue_step(c, nullptr, slot);
+  c->stream = own;
+  if (rc != GKS_OK) return rc;
+  e = cudaEventRecord(c->ev_done[k], c->s_comp);
+  c->pipe_pending = true;
+  c->pipe_last = k;
+  // copy-out after the step
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_out, c->ev_done[k], 0);
+  for (int a = 0; a < narr && e == cudaSuccess; ++a)
+    e = cudaMemcpyAsync(dst[a], slot + a * L, bytes, cudaMemcpyDeviceToHost, c->s_out);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[k], c->s_out);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline copy-out");
+  ++c->pipe_calls;
+  return GKS_OK;
+}
+
 int gks_sync(gks_ctx* c) {
   if (!c) return fail(GKS_EINVAL, "NULL context%s");
+  if (c->s_in) {
+    cudaError_t e = cudaStreamSynchronize(c->s_in);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_comp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_out);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline sync");
+  }
   return check_status(c);
 }
 
@@ -405,7 +520,20 @@ int gks_launches_per_step(gks_ctx* c) {
 
 void gks_destroy(gks_ctx* c) {
   if (!c) return;
+  if (c->s_in) cudaStreamSynchronize(c->s_in);
+  if (c->s_comp) cudaStreamSynchronize(c->s_comp);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->s_out) cudaStreamSynchronize(c->s_out);
+  for (int k = 0; k < 3; ++k) {
+    if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+    if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+    if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+  }
+  if (c->ev_ctx) cudaEventDestroy(c->ev_ctx);
+  if (c->s_in) cudaStreamDestroy(c->s_in);
+  if (c->s_comp) cudaStreamDestroy(c->s_comp);
+  if (c->s_out) cudaStreamDestroy(c->s_out);
+  if (c->slots) cudaFree(c->slots);
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   double* bufs[] = {c->state, c->stage, c->acc, c->fx, c->fy, c->d_dt};

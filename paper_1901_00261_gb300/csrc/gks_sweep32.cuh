@@ -159,7 +159,12 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
     const double dt = ldd<CG>(&tc->dt);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o64[(long)v * nfaces + face] = fma(dt, Fref[v], (double)dpsi[v]);
+      // at a wall face every flux but that of the wall-normal momentum is an odd function
+      // across the mirror and vanishes; its single-precision delta from the mirrored
+      // reference would leave ~1e-8 |rho U| instead, so the FP64 flux is set to zero there
+      // (conservation of mass, energy and tangential momentum stays exact)
+      const bool odd_at_wall = (ml || mr) && v != 1 + DIR;
+      o64[(long)v * nfaces + face] = odd_at_wall ? 0.0 : fma(dt, Fref[v], (double)dpsi[v]);
       o64[(long)(N + v) * nfaces + face] = wr[v] - wl[v];
     }
   } else {
@@ -167,7 +172,7 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       double* xi = o64 + (long)v * nfaces + face;
-      *xi = ldd<CG>(xi) + (double)(s3f * Ft[v]);
+      if (!((ml || mr) && v != 1 + DIR)) *xi = ldd<CG>(xi) + (double)(s3f * Ft[v]);
       float* lt = o32 + (1L * N + v) * nfaces + face;
       *lt = ldf<CG>(lt) + s3f * Wtt[v];
     }

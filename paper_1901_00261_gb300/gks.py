@@ -57,6 +57,7 @@ SIGNATURES = {
     "gks_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "gks_max_wavespeed": (ctypes.c_int, [ctypes.c_void_p, _DP]),
     "gks_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "gks_step_host_async": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_double]),
     "gks_state_device_ptrs": (ctypes.c_int, [ctypes.c_void_p, _DPP, _DPP, _DPP]),
     "gks_launches_per_step": (ctypes.c_int, [ctypes.c_void_p]),
     "gks_destroy": (None, [ctypes.c_void_p]),
@@ -225,6 +226,18 @@ class Solver:
         v = ctypes.c_double()
         _check(lib().gks_max_wavespeed(self._h, ctypes.byref(v)))
         return v.value
+
+    def step_host_async(self, ins, outs, dt: float):
+        """Pipelined host-to-host step (gks_step_host_async): ins = (W, Wx[, Wy]) are copied
+        in, advanced one step of dt, and written to outs = (W, Wx[, Wy]) (C-contiguous float64
+        arrays of the state's shape, ideally pinned).  Returns at once; the arrays must stay
+        alive, and outs unread, until sync()."""
+        arrs = list(ins) + [None] * (3 - len(ins)) + list(outs) + [None] * (3 - len(outs))
+        for a in arrs[:self.dim + 1] + arrs[3:4 + self.dim]:
+            if a.shape != self.shape or a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("state arrays must be C-contiguous float64 of shape %s" % (self.shape,))
+        p = [_host_ptr(a) if k % 3 <= self.dim else None for k, a in enumerate(arrs)]
+        _check(lib().gks_step_host_async(self._h, *p, float(dt)))
 
     def sync(self):
         _check(lib().gks_sync(self._h))
