@@ -26,9 +26,10 @@
 // Pins (tests/test_oracle_*.py): every function above is checked against something other
 // than itself -- printed coefficients, polynomial exactness, closed forms, quadrature, the
 // exact Euler/Navier-Stokes fluxes it must reduce to, the paper's accuracy tables, exact
-// Riemann, vortex and linear-acoustics solutions.  Whole runs of the Shu-Osher problem, the
-// shear layer and the random Riemann problems have no exact solution: for those the parity is
-// unpinned beyond conservation and positivity.
+// Riemann (including the random Riemann problems of the batched workload), vortex,
+// linear-acoustics and viscous shear-wave solutions.  Whole runs of the Shu-Osher problem and
+// the double shear layer have no exact solution: for those the parity is unpinned beyond
+// conservation, positivity and the pins of their parts.
 //
 // Readings taken where the paper is silent or garbled (each one is listed with its
 // reason in the project's design notes):

@@ -313,6 +313,32 @@ def box_pulse_2d(n: int, ny: int | None = None, gamma: float = 1.4, mu: float = 
                  order=order, recon=recon, t_end=0.5, name="box_pulse_2d")
 
 
+def shear_wave_2d(nx: int, ny: int, U0: float = 0.01, mu: float = 0.01, Pr: float = 0.72,
+                  gamma: float = 1.4, order: int = 8, recon: int = 0) -> State:
+    """Transverse viscous shear wave on periodic [0, nx/ny] x [0, 1]: rho = 1, p = 1/gamma,
+    u = U0 sin(2 pi y), v = 0.  Linearised Navier-Stokes: u decays as exp(-mu/rho (2 pi)^2 t)
+    with the pressure uniform (viscous heating enters at order U0^2)."""
+    k = 2.0 * math.pi
+
+    def pt(x, y):
+        u = U0 * np.sin(k * y) + 0.0 * x
+        one = np.ones_like(u)
+        return conservative_2d(one, u, 0.0 * u, one / gamma, gamma)
+    W, Wx, Wy = _cell_state_2d(pt, nx, ny, 0.0, nx / ny, 0.0, 1.0, gamma)
+    return State(W, Wx, Wy, nx, ny, gamma, 0.0, nx / ny, 0.0, 1.0, 0, 0, mu=mu, Pr=Pr,
+                 order=order, recon=recon, t_end=0.5, name="shear_wave_2d",
+                 meta=dict(U0=U0, k=k))
+
+
+def shear_wave_amplitude(st, W) -> float:
+    """Amplitude of the sin(2 pi y) mode of the x-momentum cell averages W[1] (projection on
+    the cell averages of sin(2 pi y))."""
+    k, h = st.meta["k"], (st.y1 - st.y0) / st.ny
+    yc = st.y0 + h * (np.arange(st.ny) + 0.5)
+    s = (np.cos(k * (yc - h / 2)) - np.cos(k * (yc + h / 2))) / (k * h)
+    return float((W[1].mean(axis=1) * s).sum() / (s * s).sum())
+
+
 def vortex_exact_avg(n: int, t: float, gamma: float = 1.4, ny: int | None = None) -> np.ndarray:
     ny = n if ny is None else ny
     W, _, _ = _cell_state_2d(lambda x, y: vortex_point(x, y, t, gamma), n, ny, 0.0, 10.0,

@@ -195,3 +195,21 @@ def test_fp32_bulk_set_state_refreshes_mirror():
     B.steps(0.01, 2)
     for a, b in zip(A.get_state(), B.get_state()):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [gks.PREC_FP64, gks.PREC_FP32_BULK], ids=["fp64", "fp32"])
+def test_viscous_shear_wave_decay_on_gpu(prec):
+    # the decay exp(-nu k^2 t) of a transverse shear wave, 64 cells across: the scheme's
+    # first-order-in-time viscous error is ~2.5e-4 here (7e-4 at 16 cells on the oracle)
+    st = inputs.shear_wave_2d(16, 64)
+    S = gks.Solver.from_state(st, precision=prec)
+    t, T = 0.0, st.t_end
+    while t < T - 1e-14:
+        dt = min(0.3 / S.max_wavespeed(), T - t)
+        S.step(dt)
+        t += dt
+    W = S.get_state()[0]
+    ratio = inputs.shear_wave_amplitude(st, W) / inputs.shear_wave_amplitude(st, st.W)
+    exact = math.exp(-st.mu * st.meta["k"] ** 2 * T)
+    assert abs(ratio / exact - 1.0) < 4e-4, ratio / exact - 1.0
+

@@ -157,6 +157,12 @@ def test_2d_navier_stokes_shear_layer():
     one_step_parity(st, nsteps=2)
 
 
+def test_2d_navier_stokes_linear_shear_wave():
+    # linear reconstruction with the Chapman-Enskog bracket (no WENO-Z): the viscous path
+    # alone, on a grid 8 cells wide with 32 across the wave
+    one_step_parity(inputs.shear_wave_2d(8, 32), nsteps=2)
+
+
 def test_2d_transmissive_boundaries():
     st = inputs.isentropic_vortex_2d(33, order=8, recon=1, ny=27)
     st.bc_x = st.bc_y = 1

@@ -1,0 +1,63 @@
+"""Whole-run physics pins of the oracle on workloads without a closed-form solution of the
+scheme itself.
+
+1. Viscous shear wave (Navier-Stokes path): u = U0 sin(k y) between periodic boundaries
+   decays as exp(-nu k^2 t) (linearised equations, uniform pressure).  The scheme as read
+   takes the time derivatives of the equilibrium state from the Euler compatibility
+   condition, which vanishes for this flow, so within a step the viscous flux is held at its
+   start value: the decay is first-order accurate in time, about (nu k^2)^2 T dt / 2 relative
+   (7e-4 at 16 cells across).  The pin is that bound and its halving under refinement; a
+   wrong viscosity (mu/p in the bracket, or its factor) or a dropped bracket term misses the
+   decay by tens of percent.
+2. Random Riemann problems of the batched workload (seeded states rho, p ~ U(0.1, 2),
+   u ~ U(-1, 1) per side, 6th or 8th order WENO-Z) against their exact solutions: the L1
+   density error at 200 cells below 1e-2 (measured up to 4.7e-3) and smaller than at 100
+   cells.  A sign or flux mistake gives errors of order 0.1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_00261_gb300 import inputs
+
+from riemann_exact import cell_average_density
+
+
+def _run(st, T):
+    O = oracle.Solver(st.nx, st.ny, st.gamma, st.mu, st.Pr, st.order, st.recon, st.bc_x,
+                      st.bc_y, st.x0, st.x1, st.y0, st.y1)
+    O.set_state(st.W, st.Wx, st.Wy)
+    t = 0.0
+    while t < T - 1e-14:
+        dt = min(0.3 / O.max_wavespeed(), T - t)
+        O.step(dt)
+        t += dt
+    return O.get_state()[0]
+
+
+def test_viscous_shear_wave_decays_at_nu_k2():
+    errs = []
+    for ny in (16, 32):
+        st = inputs.shear_wave_2d(8, ny)
+        W = _run(st, st.t_end)
+        ratio = inputs.shear_wave_amplitude(st, W) / inputs.shear_wave_amplitude(st, st.W)
+        exact = math.exp(-st.mu * st.meta["k"] ** 2 * st.t_end)
+        errs.append(abs(ratio / exact - 1.0))
+        # no motion across the layers and the density stays uniform to order U0^2
+        assert np.abs(W[2]).max() < 1e-5 and np.abs(W[0] - 1.0).max() < 1e-4
+    assert errs[0] < 2e-3, errs
+    assert errs[1] < errs[0] / 1.5, errs
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_random_riemann_problems_against_exact(k):
+    sp = [s for s in inputs.batch_specs(512, seed=0) if s.kind == "riemann_1d"][k]
+    l1 = []
+    for N in (100, 200):
+        st = inputs.riemann_1d(N, sp.left, sp.right, 0.0, 1.0, 0.5, 1.4, sp.order, 1, 0.1)
+        rho = _run(st, 0.1)[0, 0]
+        ex = cell_average_density(N, 0.0, 1.0, 0.5, 0.1, sp.left, sp.right)
+        l1.append(np.abs(rho - ex).mean())
+    assert l1[1] < 1e-2 and l1[1] < l1[0], l1
