@@ -144,6 +144,15 @@ int gks_launches_per_step(gks_ctx* ctx);
  * FP64 (fp64 != 0) or FP32; the denominator of the ALU roofline. */
 int gks_steps_timed(gks_ctx* ctx, double dt, int nsteps, double* kernel_ms);
 int gks_probe_alu_peak(int fp64, double* flops_per_s);
+/* Test probe of the non-equilibrium time-integration coefficients (Sec. 2.2: the branch
+ * e^{-t/tau} integrated over [0, dt/2] and [0, dt] and fitted linearly in t), evaluated on
+ * the device in FP64 exactly as the face kernels form them: for theta[i] = tau/dt > 0
+ * (host array, n >= 0 entries), out[4 i + 0..3] (host array) = a0, a1, b0, b1, where with
+ * E0(d) = int_0^d e^{-t/tau} dt and E1(d) = int_0^d t e^{-t/tau} dt,
+ * a0 = (4 E0(dt/2) - E0(dt))/dt, a1 = (4 E1(dt/2) - E1(dt))/dt,
+ * b0 = 4 (E0(dt) - 2 E0(dt/2))/dt^2, b1 = 4 (E1(dt) - 2 E1(dt/2))/dt^2.  Synchronous;
+ * GKS_EINVAL for a NULL array, n < 0, dt or a theta not finite and > 0. */
+int gks_probe_time_coefs(const double* theta, int n, double dt, double* out);
 
 /* Release everything the context owns.  NULL is ignored. */
 void gks_destroy(gks_ctx* ctx);

@@ -406,6 +406,17 @@ int gks_steps_timed(gks_ctx* c, double dt, int nsteps, double* kernel_ms) {
   return rc;
 }
 
+int gks_probe_time_coefs(const double* theta, int n, double dt, double* out) {
+  if (!theta || !out || n < 0) return fail(GKS_EINVAL, "NULL argument or n < 0%s");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(GKS_EINVAL, "dt must be finite and > 0%s");
+  for (int i = 0; i < n; ++i)
+    if (!(theta[i] > 0.0) || !std::isfinite(theta[i])) return fail(GKS_EINVAL, "theta must be finite and > 0%s");
+  if (n == 0) return GKS_OK;
+  cudaError_t e = gks::probe_time_coefs(theta, n, dt, out);
+  if (e != cudaSuccess) return cuda_fail(e, "time coefficient probe");
+  return GKS_OK;
+}
+
 int gks_probe_alu_peak(int fp64, double* flops_per_s) {
   if (!flops_per_s) return fail(GKS_EINVAL, "NULL argument%s");
   cudaError_t e = gks::probe_fma(fp64, 1 << 14, flops_per_s, nullptr);

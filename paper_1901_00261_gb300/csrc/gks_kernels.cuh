@@ -93,5 +93,6 @@ cudaError_t launch_wavespeed(const double* W, int nx, int ny, int dim, double ga
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
 cudaError_t launch_set_times(StepTimes* p, double dt, cudaStream_t s);
 cudaError_t probe_fma(int fp64, int iters, double* flops, cudaStream_t s);
+cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out);
 
 }  // namespace gks

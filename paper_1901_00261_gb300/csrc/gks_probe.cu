@@ -1,8 +1,41 @@
 // gks_probe.cu -- arithmetic-throughput probe used as the roofline denominator of the
-// ALU-bound face sweeps: independent FMA chains in every thread of a full grid.
+// ALU-bound face sweeps (independent FMA chains in every thread of a full grid), and a probe
+// that evaluates the face kernels' FP64 time-integration coefficients for tests.
 #include <cuda_runtime.h>
 
+#include "gks_device.cuh"
+
 namespace gks {
+
+// time_coefs(theta, 1/(2 theta), dt) for theta[i], as the non-equilibrium branch of the face
+// kernels forms it (FP64 path); out[4 i ..] = a0, a1, b0, b1.
+__global__ void time_coefs_probe_kernel(const double* theta, int n, double dt, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double th = theta[i];
+  const TimeCoef T = time_coefs(th, 0.5 / th, dt);
+  out[4 * i + 0] = T.a0;
+  out[4 * i + 1] = T.a1;
+  out[4 * i + 2] = T.b0;
+  out[4 * i + 3] = T.b1;
+}
+
+// Host arrays theta[n] and out[4 n]; synchronous.
+cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out) {
+  double* d_theta = nullptr;
+  double* d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_theta, (size_t)n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d_theta, theta, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    time_coefs_probe_kernel<<<(n + 127) / 128, 128>>>(d_theta, n, dt, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost);
+  if (d_theta) cudaFree(d_theta);
+  if (d_out) cudaFree(d_out);
+  return e;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_probe_kernel(T* out, int iters, T a, T b) {

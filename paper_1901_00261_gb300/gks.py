@@ -63,6 +63,7 @@ SIGNATURES = {
     "gks_destroy": (None, [ctypes.c_void_p]),
     "gks_steps_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _DP]),
     "gks_probe_alu_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
+    "gks_probe_time_coefs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
     "gks_step_1d_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -264,6 +265,16 @@ def probe_alu_peak(fp64: bool = True) -> float:
     v = ctypes.c_double()
     _check(lib().gks_probe_alu_peak(1 if fp64 else 0, ctypes.byref(v)))
     return v.value
+
+
+def probe_time_coefs(theta, dt: float) -> np.ndarray:
+    """The face kernels' FP64 time-integration coefficients (a0, a1, b0, b1) for each
+    theta = tau/dt, evaluated on the device (gks_probe_time_coefs); shape (n, 4)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    out = np.zeros((th.size, 4))
+    _check(lib().gks_probe_time_coefs(th.ctypes.data_as(_DP), th.size, float(dt),
+                                      out.ctypes.data_as(_DP)))
+    return out
 
 
 def _bcheck(rc: int):

@@ -1,0 +1,75 @@
+"""The face kernels' FP64 time-integration coefficients (gks_probe_time_coefs: the device
+function itself) against their definition evaluated with 80 significant digits.
+
+The non-equilibrium branch of Eq. 3rd-simplify-flux decays as e^{-t/tau}; its time integrals
+E0(d) = int_0^d e^{-t/tau} dt = tau (1 - e^{-d/tau}) and
+E1(d) = int_0^d t e^{-t/tau} dt = tau^2 (1 - e^{-d/tau} (1 + d/tau)) over [0, dt/2] and
+[0, dt], fitted linearly in t (Sec. 2.2), give the coefficients
+a0 = (4 E0(dt/2) - E0(dt))/dt, a1 = (4 E1(dt/2) - E1(dt))/dt,
+b0 = 4 (E0(dt) - 2 E0(dt/2))/dt^2, b1 = 4 (E1(dt) - 2 E1(dt/2))/dt^2.
+Each is a difference of terms of similar size; the error is measured against the size of
+those terms (for b1, which changes sign near dt/(2 tau) = 1.26, a relative error would
+be meaningless there) and must stay below 1e-14 for theta = tau/dt from 1e-8 to 1e8,
+across both branches of the device function (series below dt/(2 tau) = 1/2, closed form
+above, e^{-x} = 0 beyond 40).  The reference uses the standard library's decimal module.
+"""
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+from paper_1901_00261_gb300 import gks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gks.lib()
+
+
+def reference(theta, dt):
+    getcontext().prec = 80
+    th, D = Decimal(float(theta)), Decimal(float(dt))
+    tau = th * D
+
+    def phi(y):
+        return 1 - (-y).exp() * (1 + y)
+
+    def E0(d):
+        return tau * (1 - (-d / tau).exp())
+
+    def E1(d):
+        return tau * tau * phi(d / tau)
+
+    h = D / 2
+    x = h / tau
+    val = [(4 * E0(h) - E0(D)) / D, (4 * E1(h) - E1(D)) / D,
+           4 * (E0(D) - 2 * E0(h)) / (D * D), 4 * (E1(D) - 2 * E1(h)) / (D * D)]
+    scale = [4 * E0(h) / D, th * th * D * (4 * phi(x) + phi(2 * x)),
+             4 * (E0(D) + 2 * E0(h)) / (D * D), 4 * th * th * (phi(2 * x) + 2 * phi(x))]
+    return val, scale
+
+
+THETAS = np.concatenate([np.logspace(-8, 8, 161),
+                         [1 / 80 * (1 - 1e-9), 1 / 80 * (1 + 1e-9), 0.398, 0.4,
+                          1.0 - 1e-12, 1.0, 1.0 + 1e-12, 0.3, 0.7, 2.0]])
+
+
+@pytest.mark.parametrize("dt", [1e-3, 0.25])
+def test_time_coefficients_match_their_definition(dt):
+    got = gks.probe_time_coefs(THETAS, dt)
+    worst = 0.0
+    for th, row in zip(THETAS, got):
+        val, scale = reference(th, dt)
+        for g, v, s in zip(row, val, scale):
+            worst = max(worst, float(abs(Decimal(float(g)) - v) / s))
+    assert worst < 1e-14, worst
+
+
+def test_time_coefficient_probe_rejects_bad_theta():
+    with pytest.raises(gks.GksError):
+        gks.probe_time_coefs(np.array([1.0, 0.0]), 0.1)
