@@ -9,6 +9,10 @@ scheme itself.
    (7e-4 at 16 cells across).  The pin is that bound and its halving under refinement; a
    wrong viscosity (mu/p in the bracket, or its factor) or a dropped bracket term misses the
    decay by tens of percent.
+   The same wave without viscosity pins the two readings of the collision time in the
+   Chapman-Enskog terms (R1): with the physical time mu/p = 0 it is a steady Euler flow;
+   with the numerical time (tau_mode 1) the bracket carries tau = eps dt, i.e. a viscosity
+   eps dt p, and the wave decays as exp(-eps dt p / rho k^2 t).
 2. Random Riemann problems of the batched workload (seeded states rho, p ~ U(0.1, 2),
    u ~ U(-1, 1) per side, 6th or 8th order WENO-Z) against their exact solutions: the L1
    density error at 200 cells below 1e-2 (measured up to 4.7e-3) and smaller than at 100
@@ -49,6 +53,25 @@ def test_viscous_shear_wave_decays_at_nu_k2():
         assert np.abs(W[2]).max() < 1e-5 and np.abs(W[0] - 1.0).max() < 1e-4
     assert errs[0] < 2e-3, errs
     assert errs[1] < errs[0] / 1.5, errs
+
+
+@pytest.mark.parametrize("tau_mode", [0, 1])
+def test_inviscid_shear_wave_and_the_collision_time_reading(tau_mode):
+    st = inputs.shear_wave_2d(8, 16, mu=0.0, Pr=1.0)
+    O = oracle.Solver(st.nx, st.ny, st.gamma, 0.0, 1.0, st.order, st.recon, 0, 0, st.x0, st.x1,
+                      st.y0, st.y1, tau_mode=tau_mode)
+    O.set_state(st.W, st.Wx, st.Wy)
+    dt = 0.3 / O.max_wavespeed()
+    n = int(round(0.5 / dt))
+    for _ in range(n):
+        O.step(dt)
+    ratio = inputs.shear_wave_amplitude(st, O.get_state()[0]) / inputs.shear_wave_amplitude(st, st.W)
+    if tau_mode == 0:
+        assert abs(ratio - 1.0) < 1e-8, ratio - 1.0
+    else:
+        nu_eff = 0.01 * dt * (1.0 / st.gamma)   # eps dt p / rho, p = 1/gamma, rho = 1
+        decay = 1.0 - math.exp(-nu_eff * st.meta["k"] ** 2 * n * dt)
+        assert abs((1.0 - ratio) / decay - 1.0) < 1e-3, (1.0 - ratio, decay)
 
 
 @pytest.mark.parametrize("k", range(8))
