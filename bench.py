@@ -46,18 +46,21 @@ CFL = 0.3
 # 20 %); traffic: DRAM bytes (read + write) per unit from the 1024^2 capture, scaled to a launch
 # by the units processed (the kernels stream, so traffic grows in proportion; at 1024^2 part
 # of the data stays in L2, so it reads low).  The FP64 form has no traffic figure: its 256^2
-# capture fits in L2.
+# capture fits in L2.  winstr: executed warp-instructions per 32 units (same captures), for
+# the instruction-issue rate the sweeps are limited by (reported beside the roofline).
 KERNEL_MODEL = {
-    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2},
-    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6},
-    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2},
-    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6},
-    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0},
-    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0},
-    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 249.0},
-    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0},
-    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0},
-    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 343.0},
+    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2, "winstr": 7353},
+    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
+    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
+    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
+    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0, "winstr": 2459},
+    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0, "winstr": 2220},
+    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 249.0,
+                                "winstr": 408},
+    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0, "winstr": 1924},
+    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0, "winstr": 1717},
+    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 343.0,
+                                "winstr": 656},
 }
 HBM_FALLBACK_GBS = 6800.0
 
@@ -73,10 +76,12 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s GB300 copy bandwidth)"
 
 
-def roofline(form, name, ms, nx, ny, order, peak64, peak32):
+def roofline(form, name, ms, nx, ny, order, peak64, peak32, issue_peak=None):
     """Roofline of one launch of kernel `name` taking `ms` milliseconds: the fraction of the
     FP32 and FP64 peaks (probes measured in this run) and of the HBM bandwidth, the largest
-    named as the bound, the others listed beside it."""
+    named as the bound, the others listed beside it.  With issue_peak (warp-instructions per
+    second the SMs can issue), the launch's instruction-issue rate is listed beside them too
+    (executed instructions are not algorithmic work, so it is never the headline bound)."""
     m = KERNEL_MODEL.get((form, name)) if order == 8 else None
     if m is None:
         return {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
@@ -107,6 +112,11 @@ def roofline(form, name, ms, nx, ny, order, peak64, peak32):
     main["kernel"] = name
     main["traffic"] = m["traffic"] * units if m.get("traffic") else None
     main["other_bounds"] = [{k: c[k] for k in ("bound", "achieved", "peak", "unit", "frac")} for c in cands[1:]]
+    if issue_peak and m.get("winstr"):
+        a = m["winstr"] / 32.0 * units / sec
+        main["other_bounds"].append({"bound": "issue", "achieved": a / 1e9, "peak": issue_peak / 1e9,
+                                     "unit": "G warp-instructions/s", "frac": a / issue_peak,
+                                     "peak_source": "4 per clock per SM x SMs x median SM clock under load"})
     return main
 
 
@@ -477,9 +487,18 @@ def main():
         per_launch = kernel_ms / args.steps
         k_dom = int(np.argmax(per_launch))
         name = slot_names[k_dom]
-        roof = roofline(form, name, float(per_launch[k_dom]), st.nx, st.ny, args.order, peak64, peak32)
+        csum = clk.summary()
+        issue_peak = None
+        try:
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            mhz = csum.get("sm_mhz") or 2070.0
+            issue_peak = 4.0 * sms * mhz * 1e6
+        except Exception:
+            issue_peak = None
+        roof = roofline(form, name, float(per_launch[k_dom]), st.nx, st.ny, args.order, peak64, peak32,
+                        issue_peak)
         r = {"value": value, "ms_per_step": ms / args.steps,
-             "gpu_launches": nl * args.steps, "roofline": roof, "clocks": clk.summary(),
+             "gpu_launches": nl * args.steps, "roofline": roof, "clocks": csum,
              "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}
         if not args.no_acc and rank == 0:
             T = dt * (args.warmup + args.steps)
