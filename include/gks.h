@@ -16,12 +16,14 @@
  *   - Host state arrays are C-contiguous float64 [nvar][ny][nx], nvar = 3 (1D, ny == 1)
  *     or 4 (2D).  Gradients are dimensional (dW/dx averaged over the cell).
  *   - The caller owns every buffer it passes; the library owns its device buffers
- *     (allocated with cudaMalloc on the current device at gks_create, freed by
- *     gks_destroy).
+ *     (allocated with cudaMalloc on the current device at gks_create, and at the first
+ *     gks_step_host_async for its pipeline slots; freed by gks_destroy).
  *   - Every int-returning call returns GKS_OK (0) or a negative gks_status; the message
  *     of the last error on the calling thread is available from gks_last_error().
  *   - Device work runs on the context's stream (opts.stream, or a stream the library
- *     creates).  Conditions detected on the device (a non-physical interface state) are
+ *     creates); gks_step_host_async also runs on three streams of its own, ordered with
+ *     the context stream by events.  Conditions detected on the device (a non-physical
+ *     interface state) are
  *     reported by the next synchronising call (gks_get_state*, gks_sync,
  *     gks_max_wavespeed) as GKS_ENONPHYSICAL.
  */
