@@ -23,9 +23,8 @@
  *   - Device work runs on the context's stream (opts.stream, or a stream the library
  *     creates); gks_step_host_async also runs on three streams of its own, ordered with
  *     the context stream by events.  Conditions detected on the device (a non-physical
- *     interface state) are
- *     reported by the next synchronising call (gks_get_state*, gks_sync,
- *     gks_max_wavespeed) as GKS_ENONPHYSICAL.
+ *     interface state) are reported by the next synchronising call (gks_get_state*,
+ *     gks_sync, gks_max_wavespeed) as GKS_ENONPHYSICAL.
  */
 #ifndef GKS_GB300_H
 #define GKS_GB300_H
