@@ -41,10 +41,13 @@ def _run(st, T):
     return O.get_state()[0]
 
 
-def test_viscous_shear_wave_decays_at_nu_k2():
+@pytest.mark.parametrize("recon,drop", [(0, 1.5), (1, 1.3)])
+def test_viscous_shear_wave_decays_at_nu_k2(recon, drop):
+    # recon 1: the WENO-Z path, whose non-equilibrium branch runs with tau = mu/p (measured
+    # 6.2e-4 at 16 cells and 3.9e-4 at 32; the linear path 1.0e-3 and 5.0e-4)
     errs = []
     for ny in (16, 32):
-        st = inputs.shear_wave_2d(8, ny)
+        st = inputs.shear_wave_2d(8, ny, recon=recon)
         W = _run(st, st.t_end)
         ratio = inputs.shear_wave_amplitude(st, W) / inputs.shear_wave_amplitude(st, st.W)
         exact = math.exp(-st.mu * st.meta["k"] ** 2 * st.t_end)
@@ -52,7 +55,7 @@ def test_viscous_shear_wave_decays_at_nu_k2():
         # no motion across the layers and the density stays uniform to order U0^2
         assert np.abs(W[2]).max() < 1e-5 and np.abs(W[0] - 1.0).max() < 1e-4
     assert errs[0] < 2e-3, errs
-    assert errs[1] < errs[0] / 1.5, errs
+    assert errs[1] < errs[0] / drop, errs
 
 
 @pytest.mark.parametrize("tau_mode", [0, 1])
