@@ -330,6 +330,37 @@ def shear_wave_2d(nx: int, ny: int, U0: float = 0.01, mu: float = 0.01, Pr: floa
                  meta=dict(U0=U0, k=k))
 
 
+def entropy_wave_2d(nx: int, ny: int, delta: float = 0.01, mu: float = 0.01, Pr: float = 0.72,
+                    gamma: float = 1.4, order: int = 8, recon: int = 0) -> State:
+    """Static entropy (temperature) wave on periodic [0, nx/ny] x [0, 1]: rho = 1 +
+    delta sin(2 pi y), p = 1/gamma, u = v = 0.  Linearised Navier-Stokes: the entropy
+    perturbation p'/p - gamma rho'/rho decays by heat conduction as exp(-chi (2 pi)^2 t),
+    chi = kappa / (rho c_p) = mu / (rho Pr), up to corrections of second order in chi."""
+    k = 2.0 * math.pi
+
+    def pt(x, y):
+        rho = 1.0 + delta * np.sin(k * y) + 0.0 * x
+        zero = 0.0 * rho
+        return conservative_2d(rho, zero, zero, np.full_like(rho, 1.0 / gamma), gamma)
+    W, Wx, Wy = _cell_state_2d(pt, nx, ny, 0.0, nx / ny, 0.0, 1.0, gamma)
+    return State(W, Wx, Wy, nx, ny, gamma, 0.0, nx / ny, 0.0, 1.0, 0, 0, mu=mu, Pr=Pr,
+                 order=order, recon=recon, t_end=0.5, name="entropy_wave_2d", meta=dict(k=k))
+
+
+def entropy_wave_amplitude(st, W) -> float:
+    """Amplitude of the sin(2 pi y) mode of the entropy perturbation p'/p0 - gamma rho'/rho0
+    of the cell averages W (rho0 = 1, p0 = 1/gamma), projected as in shear_wave_amplitude."""
+    g = st.gamma
+    rho = W[0]
+    u, v = W[1] / rho, W[2] / rho
+    p = (g - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v))
+    s_prime = (p - 1.0 / g) * g - g * (rho - 1.0)
+    k, h = st.meta["k"], (st.y1 - st.y0) / st.ny
+    yc = st.y0 + h * (np.arange(st.ny) + 0.5)
+    s = (np.cos(k * (yc - h / 2)) - np.cos(k * (yc + h / 2))) / (k * h)
+    return float((s_prime.mean(axis=1) * s).sum() / (s * s).sum())
+
+
 def shear_wave_amplitude(st, W) -> float:
     """Amplitude of the sin(2 pi y) mode of the x-momentum cell averages W[1] (projection on
     the cell averages of sin(2 pi y))."""

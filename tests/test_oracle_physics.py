@@ -13,6 +13,11 @@ scheme itself.
    Chapman-Enskog terms (R1): with the physical time mu/p = 0 it is a steady Euler flow;
    with the numerical time (tau_mode 1) the bracket carries tau = eps dt, i.e. a viscosity
    eps dt p, and the wave decays as exp(-eps dt p / rho k^2 t).
+   A static entropy wave pins the heat conduction, Prandtl-number fix included (R10): its
+   entropy perturbation decays as exp(-mu/(rho Pr) k^2 t).  What remains is second order in
+   the diffusivity (it drops 4x when mu halves and grows as 1/Pr^2; measured 4.8e-3 at
+   mu = 0.01, Pr = 1 and 9.2e-3 at Pr = 0.72), whereas a conductivity off by a factor, or
+   the fix left out (8 % at Pr = 0.72), shows at first order.
 2. Random Riemann problems of the batched workload (seeded states rho, p ~ U(0.1, 2),
    u ~ U(-1, 1) per side, 6th or 8th order WENO-Z) against their exact solutions: the L1
    density error at 200 cells below 1e-2 (measured up to 4.7e-3) and smaller than at 100
@@ -56,6 +61,23 @@ def test_viscous_shear_wave_decays_at_nu_k2(recon, drop):
         assert np.abs(W[2]).max() < 1e-5 and np.abs(W[0] - 1.0).max() < 1e-4
     assert errs[0] < 2e-3, errs
     assert errs[1] < errs[0] / drop, errs
+
+
+def _entropy_decay_error(mu, Pr):
+    st = inputs.entropy_wave_2d(8, 16, mu=mu, Pr=Pr)
+    W = _run(st, st.t_end)
+    ratio = inputs.entropy_wave_amplitude(st, W) / inputs.entropy_wave_amplitude(st, st.W)
+    return ratio / math.exp(-mu / Pr * st.meta["k"] ** 2 * st.t_end) - 1.0
+
+
+def test_entropy_wave_decays_by_heat_conduction():
+    d1, d2 = _entropy_decay_error(0.01, 1.0), _entropy_decay_error(0.005, 1.0)
+    d3 = _entropy_decay_error(0.01, 0.72)
+    assert abs(d1) < 2e-2 and abs(d3) < 2e-2, (d1, d3)
+    # second order in the diffusivity chi = mu / Pr: a factor 4 for mu / 2 (2 at first
+    # order) and 1/0.72^2 = 1.93 for Pr 0.72
+    assert abs(d2) < abs(d1) / 2.8, (d1, d2)
+    assert 1.5 < d3 / d1 < 2.5, (d1, d3)
 
 
 @pytest.mark.parametrize("tau_mode", [0, 1])
