@@ -148,18 +148,29 @@ def test_transposed_problem_gives_transposed_solution(recon, mu, bcx, bcy):
             assert np.abs(got[v] - want[v]).max() <= 1e-12 * scale, (v, h)
 
 
-def _sound_attenuation_coefficient(mu, Pr, N=40, U0=1e-3, T=1.0):
+def _sound_attenuation_coefficient(mu, Pr, dim=1, N=40, U0=1e-3, T=1.0):
     """Standing sound wave u = U0 sin(2 pi x) on the periodic [0, 1] (rho = 1, c = 1), one
-    period: the amplitude of the rho U mode falls by exp(-C mu k^2 T / 2); returns C."""
+    period: the amplitude of the momentum mode falls by exp(-C mu k^2 T / 2); returns C.
+    dim 2: the same wave along y on an 8 x N grid (v = U0 sin(2 pi y))."""
     g, k = 1.4, 2.0 * math.pi
-    f = lambda x: (np.ones_like(x), U0 * np.sin(k * x), np.full_like(x, 1.0 / g))  # noqa: E731
-    W, Wx = inputs.cell_state_1d([(0.0, 1.0, f)], N, 0.0, 1.0, g)
-    O = oracle.Solver(N, 1, g, mu, Pr, 8, 0, 0, 0, 0.0, 1.0)
-    O.set_state(W, Wx, None)
     h = 1.0 / N
     xc = (np.arange(N) + 0.5) * h
     s = (np.cos(k * (xc - h / 2)) - np.cos(k * (xc + h / 2))) / (k * h)
-    amp = lambda Wc: (Wc[1][0] * s).sum() / (s * s).sum()  # noqa: E731
+    if dim == 1:
+        f = lambda x: (np.ones_like(x), U0 * np.sin(k * x), np.full_like(x, 1.0 / g))  # noqa: E731
+        W, Wx = inputs.cell_state_1d([(0.0, 1.0, f)], N, 0.0, 1.0, g)
+        Wy = None
+        O = oracle.Solver(N, 1, g, mu, Pr, 8, 0, 0, 0, 0.0, 1.0)
+        amp = lambda Wc: (Wc[1][0] * s).sum() / (s * s).sum()  # noqa: E731
+    else:
+        def pt(x, y):
+            one = np.ones(np.broadcast(x, y).shape)
+            v = U0 * np.sin(k * y) + 0.0 * x
+            return inputs.conservative_2d(one, 0.0 * v, v, one / g, g)
+        W, Wx, Wy = inputs._cell_state_2d(pt, 8, N, 0.0, 8.0 / N, 0.0, 1.0, g)
+        O = oracle.Solver(8, N, g, mu, Pr, 8, 0, 0, 0, 0.0, 8.0 / N, 0.0, 1.0)
+        amp = lambda Wc: (Wc[2].mean(axis=1) * s).sum() / (s * s).sum()  # noqa: E731
+    O.set_state(W, Wx, Wy)
     a0 = amp(W)
     ns = math.ceil(T / (0.3 / O.max_wavespeed()))
     for _ in range(ns):
@@ -167,18 +178,21 @@ def _sound_attenuation_coefficient(mu, Pr, N=40, U0=1e-3, T=1.0):
     return -2.0 * math.log(amp(O.get_state()[0]) / a0) / (mu * k * k)
 
 
+@pytest.mark.parametrize("dim", [1, 2])
 @pytest.mark.parametrize("Pr", [1e6, 1.0, 0.72])
-def test_1d_sound_attenuation(Pr):
-    # Sound in the 1D gas of the scheme (K = 4 internal degrees of freedom at gamma = 1.4)
-    # is damped by the longitudinal viscosity and by heat conduction: the amplitude decays
-    # at (k^2 / 2 rho) (mu_L + (gamma - 1) kappa / c_p).  For the BGK model the first-order
-    # momentum-flux correction at rest is -tau (p_t + (3 p U)_x) = -tau p (3 - gamma) U_x,
-    # i.e. mu_L = 2K/(K+1) mu = 1.6 mu; kappa / c_p = mu / Pr with the Prandtl fix.  So
-    # C = 1.6 + 0.4 / Pr: 1.6 without conduction (Pr = 1e6), 2.0 at Pr = 1, 2.156 at 0.72.
-    # Measured at 40 cells: 1.586 / 1.985 / 2.136 for mu = 0.01 and 1.592 / 1.991 / 2.144 for
-    # mu = 0.005 (the remainder shrinks with mu).  Finer grids at this mu exceed the explicit
-    # step's diffusion limit.
+def test_sound_attenuation(Pr, dim):
+    # Sound is damped by the longitudinal viscosity and by heat conduction: the amplitude
+    # decays at (k^2 / 2 rho) (mu_L + (gamma - 1) kappa / c_p).  For the BGK model the
+    # first-order momentum-flux correction at rest is -tau (p_t + (3 p U)_x) =
+    # -tau p (3 - gamma) U_x, i.e. mu_L = (3 - gamma) mu = 1.6 mu at gamma = 1.4 in 1D
+    # (K = 4 internal degrees of freedom: 2K/(K+1)) and in 2D alike; kappa / c_p = mu / Pr
+    # with the Prandtl fix.  So C = 1.6 + 0.4 / Pr: 1.6 without conduction (Pr = 1e6), 2.0 at
+    # Pr = 1, 2.156 at 0.72.  Measured with 40 cells across the wave, 1D: 1.586 / 1.985 /
+    # 2.136 for mu = 0.01 and 1.592 / 1.991 / 2.144 for mu = 0.005; 2D: 1.593 / 1.993 / 2.145
+    # and 1.597 / 1.996 / 2.151 (the remainder shrinks with mu).  Finer grids at this mu
+    # exceed the explicit step's diffusion limit.
     expect = 1.6 + 0.4 / Pr
-    c1, c2 = _sound_attenuation_coefficient(0.01, Pr), _sound_attenuation_coefficient(0.005, Pr)
+    c1 = _sound_attenuation_coefficient(0.01, Pr, dim)
+    c2 = _sound_attenuation_coefficient(0.005, Pr, dim)
     assert abs(c2 / expect - 1.0) < 1e-2, (c2, expect)
     assert abs(c2 - expect) < abs(c1 - expect), (c1, c2, expect)
