@@ -26,10 +26,12 @@
 // Pins (tests/test_oracle_*.py): every function above is checked against something other
 // than itself -- printed coefficients, polynomial exactness, closed forms, quadrature, the
 // exact Euler/Navier-Stokes fluxes it must reduce to, the paper's accuracy tables, exact
-// Riemann (including the random Riemann problems of the batched workload), vortex,
-// linear-acoustics and viscous shear-wave solutions.  Whole runs of the Shu-Osher problem and
-// the double shear layer have no exact solution: for those the parity is unpinned beyond
-// conservation, positivity and the pins of their parts.
+// Riemann (including the random Riemann problems of the batched workload), vortex and
+// linear-acoustics solutions, the linearised Navier-Stokes decay of shear, entropy and sound
+// waves (viscosity, heat conduction with the Prandtl fix, 1D and 2D), the mirror symmetry of
+// reflecting walls and the rotational symmetry of the 2D scheme.  Whole runs of the Shu-Osher
+// problem and the double shear layer have no exact solution: for those the parity is
+// unpinned beyond conservation, positivity and the pins of their parts.
 //
 // Readings taken where the paper is silent or garbled (each one is listed with its
 // reason in the project's design notes):
