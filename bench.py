@@ -282,6 +282,31 @@ def cpu_baseline(st, dt, budget_s=12.0, window=128, keep=None):
             "sample": f"{w}x{w} window at the centre of the {st.nx}x{st.ny} workload, {steps} steps, {el:.1f} s"}
 
 
+def cpu_single_thread(st, dt, budget_s=4.0, window=64):
+    """The oracle on one host thread, on a smaller window of the same workload (the
+    per-core rate beside the all-core cpu_baseline)."""
+    import oracle
+    threads = oracle.get_threads()
+    oracle.set_threads(1)
+    try:
+        ws = window_state(st, window)
+        O = oracle.Solver(ws.nx, ws.ny, ws.gamma, ws.mu, ws.Pr, ws.order, ws.recon, 1, 1,
+                          ws.x0, ws.x1, ws.y0, ws.y1)
+        O.set_state(ws.W, ws.Wx, ws.Wy)
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            O.step(dt)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s or steps >= 50:
+                break
+    finally:
+        oracle.set_threads(threads)
+    return {"value": ws.nx * ws.ny * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ws.nx}x{ws.ny} window at the centre, {steps} steps, {el:.1f} s"}
+
+
 def vs_oracle(keep, dt, forms):
     """Both GPU forms on the oracle's window problem, same dt and step count: the L1 density
     difference and the largest per-variable difference relative to max |W| (cell averages)."""
@@ -577,6 +602,7 @@ def main():
         if not args.no_cpu and ws == 1:
             keep = {}
             line["cpu_baseline"] = cpu_baseline(st, dt, keep=keep)
+            line["cpu_baseline"]["single_thread"] = cpu_single_thread(st, dt)
             line["vs_oracle"] = vs_oracle(keep, dt, forms)
         print(json.dumps(line), flush=True)
     for form in forms:

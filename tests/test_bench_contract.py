@@ -46,3 +46,12 @@ def test_oracle_window_is_the_centre_of_the_workload():
     assert math.isclose(w.x1 - w.x0, 16 * st.dx) and math.isclose(w.y1 - w.y0, 16 * st.dy)
     assert np.array_equal(w.W, st.W[:, 24:40, 24:40])
     assert np.array_equal(w.Wy, st.Wy[:, 24:40, 24:40])
+
+
+def test_single_thread_oracle_sample_restores_the_thread_count():
+    import oracle
+    before = oracle.get_threads()
+    st = inputs.isentropic_vortex_2d(32)
+    r = bench.cpu_single_thread(st, 0.01, budget_s=0.05, window=16)
+    assert r["cores"] == 1 and r["value"] > 0 and r["kind"] == "oracle"
+    assert oracle.get_threads() == before
