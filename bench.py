@@ -602,7 +602,10 @@ def main():
         if not args.no_cpu and ws == 1:
             keep = {}
             line["cpu_baseline"] = cpu_baseline(st, dt, keep=keep)
-            line["cpu_baseline"]["single_thread"] = cpu_single_thread(st, dt)
+            try:
+                line["cpu_baseline"]["single_thread"] = cpu_single_thread(st, dt)
+            except Exception as e:  # an auxiliary figure: never lose the line over it
+                line["cpu_baseline"]["single_thread"] = {"unavailable": f"{type(e).__name__}: {e}"}
             line["vs_oracle"] = vs_oracle(keep, dt, forms)
         print(json.dumps(line), flush=True)
     for form in forms:
