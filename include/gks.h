@@ -63,7 +63,8 @@ typedef struct gks_opts {
   double x0, x1, y0, y1;   /* domain; dx = (x1 - x0)/nx, dy = (y1 - y0)/ny */
   int bc_x, bc_y;          /* GKS_BC_PERIODIC, GKS_BC_TRANSMISSIVE or GKS_BC_REFLECTING */
   int precision;           /* GKS_PREC_FP64 or GKS_PREC_FP32_BULK */
-  double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-12 */
+  double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-6 (the
+                              paper prints none; 1e-6 reproduces Tables 3-4 of Sec. 4.1) */
   double eps_tau, C_tau;   /* numerical collision time eps*dt + C|pl-pr|/(pl+pr) dt of Sec. 4;
                               defaults 0.01 and 1 */
   int use_graph;           /* 1: replay the two-stage step as a captured CUDA graph */
@@ -74,7 +75,7 @@ typedef struct gks_opts {
   void* stream;            /* cudaStream_t to run on; NULL: the library creates one */
 } gks_opts;
 
-/* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-12,
+/* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-6,
  * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL. */
 void gks_default_opts(gks_opts* o);
 

@@ -79,6 +79,7 @@ def lib():
             L.orc_create.restype = c_void
             L.orc_destroy.argtypes = [c_void]
             L.orc_set_eq_mode.argtypes = [c_void, c_int]
+            L.orc_set_char_mode.argtypes = [c_void, c_int]
             L.orc_set_state.argtypes = [c_void, dp, dp, dp]
             L.orc_get_state.argtypes = [c_void, dp, dp, dp]
             L.orc_step.argtypes = [c_void, c_double]
@@ -126,7 +127,7 @@ def smoothness(c, deg: int) -> float:
     return float(lib().orc_smoothness(_p(buf), int(deg)))
 
 
-def weno_left(order: int, in8, eps: float = 1e-12):
+def weno_left(order: int, in8, eps: float = 1e-6):
     """Returns (value, d/ds, delta[7], beta[7]) of the WENO-Z left state (Sec. 3.3)."""
     x = np.ascontiguousarray(np.asarray(in8, dtype=np.float64))
     out = np.zeros(16)
@@ -134,7 +135,7 @@ def weno_left(order: int, in8, eps: float = 1e-12):
     return out[0], out[1], out[2:9].copy(), out[9:16].copy()
 
 
-def weno_right(order: int, in8, eps: float = 1e-12):
+def weno_right(order: int, in8, eps: float = 1e-6):
     x = np.ascontiguousarray(np.asarray(in8, dtype=np.float64))
     out = np.zeros(2)
     lib().orc_weno_right(order, _p(x), eps, _p(out))
@@ -218,8 +219,8 @@ class Solver:
     def __init__(self, nx: int, ny: int, gamma: float = 1.4, mu: float = 0.0, Pr: float = 1.0,
                  order: int = 6, recon: int = 0, bc_x: int = 0, bc_y: int = 0,
                  x0: float = 0.0, x1: float = 1.0, y0: float = 0.0, y1: float = 1.0,
-                 weno_eps: float = 1e-12, tau_mode: int = 0, flux_mode: int = 0,
-                 eq_mode: int = 1):
+                 weno_eps: float = 1e-6, tau_mode: int = 0, flux_mode: int = 0,
+                 eq_mode: int = 1, char_mode: int = 0):
         self.nx, self.ny = nx, ny
         self.dim = 2 if ny > 1 else 1
         self.nv = self.dim + 2
@@ -228,6 +229,7 @@ class Solver:
         if not self._h:
             raise ValueError("invalid oracle parameters")
         lib().orc_set_eq_mode(self._h, int(eq_mode))
+        lib().orc_set_char_mode(self._h, int(char_mode))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -39,7 +39,8 @@
 //       Euler equations); the exponentials use the numerical collision time of
 //       Sec. 4 (eps*dt + C|pl-pr|/(pl+pr)*dt, or mu/p + C|pl-pr|/(pl+pr)*dt).
 //       tau_mode = 1 puts the numerical time into the bracket as well.
-//   R2  WENO-Z epsilon defaults to 1e-12.
+//   R2  WENO-Z epsilon defaults to 1e-6: the value that reproduces the WENO-Z rows of
+//       Tables 3-4 (Sec. 4.1); 1e-12 misses the finer rows by up to 3x.
 //   R3  the beta constant of (a4 h^4)^2 comes from integrating the definition.
 //   R4  interface values: moments of the equilibrium branch of f at t = 0 and its
 //       first two time derivatives.
@@ -52,7 +53,8 @@
 //       fixed by the linearised compatibility chain.
 //   R7  non-equilibrium slopes: WENO-weighted candidate derivatives (w1 quadratic).
 //   R8  WENO in the characteristic variables of the normal Jacobian at the mean of
-//       the two cells adjacent to the interface.
+//       the two cells adjacent to the interface (char_mode = 1: component-wise instead,
+//       which misses Table 4 at N = 40 and 80 by 1.4 % and 6 %).
 //   R9  tangential direction: quartic through five face line-averages.
 //   R10 Prandtl fix: (1/Pr - 1) times the heat flux of the bracket terms is added
 //       to the energy flux.
@@ -662,6 +664,7 @@ void euler_right_eigvecs(int dim, double gamma, const double* W, double* R) {
 // ===========================================================================
 struct Solver {
   int nx, ny, dim, nv, order, recon, bcx, bcy;
+  int char_mode = 0;   // R8: 0 = characteristic variables at the mean state, 1 = component-wise
   double x0, x1, y0, y1, dx, dy, weno_eps;
   Phys ph;
   std::vector<double> W, Wx, Wy;   // [nv][ny][nx]
@@ -724,8 +727,19 @@ bool normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& 
     for (int v = 0; v < n; ++v) { fr.Wl[v] = fr.Wr[v] = fr.W0[v]; fr.Wln[v] = fr.Wrn[v] = fr.W0n[v]; }
     return true;
   }
-  // characteristic projection at the mean of the two cells next to the face
   double Wm[4], R[16], L[16];
+  if (S.char_mode == 1) {
+    // R8 alternative: WENO-Z on each conservative variable separately
+    for (int v = 0; v < n; ++v) {
+      double a, b;
+      weno_left(oi, in8[v], S.weno_eps, &a, &b, nullptr, nullptr);
+      fr.Wl[v] = a; fr.Wln[v] = b / h;
+      weno_right(oi, in8[v], S.weno_eps, &a, &b);
+      fr.Wr[v] = a; fr.Wrn[v] = b / h;
+    }
+    return true;
+  }
+  // characteristic projection at the mean of the two cells next to the face
   for (int v = 0; v < n; ++v) Wm[v] = 0.5 * (in8[v][1] + in8[v][2]);
   {
     double ke = 0.0;
@@ -1121,6 +1135,8 @@ void orc_destroy(void* h) { delete static_cast<Solver*>(h); }
 // Reading of the equilibrium interface value: 0 = linear compact reconstruction,
 // 1 = collision of the left/right initial states.
 void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; }
+// R8 option: 0 = WENO-Z in characteristic variables (default), 1 = component-wise.
+void orc_set_char_mode(void* h, int m) { static_cast<Solver*>(h)->char_mode = m; }
 void orc_set_state(void* h, const double* W, const double* Wx, const double* Wy) {
   Solver* S = static_cast<Solver*>(h);
   std::memcpy(S->W.data(), W, sizeof(double) * S->W.size());

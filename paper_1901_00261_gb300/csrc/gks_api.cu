@@ -203,7 +203,7 @@ void gks_default_opts(gks_opts* o) {
   o->x0 = 0; o->x1 = 1; o->y0 = 0; o->y1 = 1;
   o->bc_x = GKS_BC_PERIODIC; o->bc_y = GKS_BC_PERIODIC;
   o->precision = GKS_PREC_FP64;
-  o->weno_eps = 1e-12;
+  o->weno_eps = 1e-6;
   o->eps_tau = 0.01; o->C_tau = 1.0;
   o->use_graph = 1;
   o->tau_mode = 0;

@@ -432,7 +432,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     gks::PhysParams ph{};
     ph.gamma = q.gamma;
     ph.K = dim == 1 ? (3.0 - q.gamma) / (q.gamma - 1.0) : (4.0 - 2.0 * q.gamma) / (q.gamma - 1.0);
-    ph.mu = q.mu; ph.Pr = q.Pr; ph.eps_tau = 0.01; ph.C_tau = 1.0; ph.weno_eps = 1e-12;
+    ph.mu = q.mu; ph.Pr = q.Pr; ph.eps_tau = 0.01; ph.C_tau = 1.0; ph.weno_eps = 1e-6;
     gks::set_phys_floats(ph);
     for (int st = 0; st < 2; ++st) {
       for (int d = 0; d < 2; ++d) {
@@ -446,7 +446,7 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
         a.nx = q.nx; a.ny = q.ny; a.bcx = q.bc_x; a.bcy = q.bc_y;
         a.dn = d == 0 ? dx : dy; a.dtan = d == 0 ? dy : dx;
         a.dnf = (float)a.dn; a.itanf = (float)(1.0 / a.dtan);
-        a.gammaf = (float)q.gamma; a.epsf = 1e-12f;
+        a.gammaf = (float)q.gamma; a.epsf = 1e-6f;
         a.stage = st + 1;
         a.P = ph;
       }

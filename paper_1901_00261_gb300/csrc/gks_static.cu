@@ -103,7 +103,7 @@ extern "C" int gks_step_1d_static(const double* W, const double* Wx, double* W_o
   fa.nx = nx; fa.ny = 1; fa.bcx = bc; fa.bcy = 0;
   fa.dn = dx; fa.dtan = 1.0;
   fa.P.gamma = gamma; fa.P.K = (3.0 - gamma) / (gamma - 1.0);
-  fa.P.mu = mu; fa.P.Pr = Pr; fa.P.eps_tau = 0.01; fa.P.C_tau = 1.0; fa.P.weno_eps = 1e-12;
+  fa.P.mu = mu; fa.P.Pr = Pr; fa.P.eps_tau = 0.01; fa.P.C_tau = 1.0; fa.P.weno_eps = 1e-6;
   gks::set_phys_floats(fa.P);
   fa.out = s + OFF_FACES;
   gks::UpdateArgs ua;

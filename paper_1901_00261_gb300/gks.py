@@ -152,7 +152,7 @@ class Solver:
     def __init__(self, nx: int, ny: int = 1, gamma: float = 1.4, mu: float = 0.0, Pr: float = 1.0,
                  order: int = 6, recon: int = RECON_LINEAR, x0: float = 0.0, x1: float = 1.0,
                  y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
-                 weno_eps: float = 1e-12, use_graph: bool = True, stream=None,
+                 weno_eps: float = 1e-6, use_graph: bool = True, stream=None,
                  precision: int = PREC_FP64, tau_mode: int = 0, eps_tau: float = 0.01,
                  C_tau: float = 1.0):
         L = lib()

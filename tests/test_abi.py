@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_default_opts():
     o = gks.default_opts()
-    assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-12, 0.01, 1.0, 1)
+    assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-6, 0.01, 1.0, 1)
     assert o.tau_mode == 0 and o.stream is None
 
 
