@@ -80,6 +80,9 @@ def lib():
             L.orc_destroy.argtypes = [c_void]
             L.orc_set_eq_mode.argtypes = [c_void, c_int]
             L.orc_set_char_mode.argtypes = [c_void, c_int]
+            L.orc_set_tan_mode.argtypes = [c_void, c_int]
+            L.orc_tan_weno.argtypes = [dp, c_int, c_int, c_double, dp]
+            L.orc_tan_weno.restype = c_double
             L.orc_set_state.argtypes = [c_void, dp, dp, dp]
             L.orc_get_state.argtypes = [c_void, dp, dp, dp]
             L.orc_step.argtypes = [c_void, c_double]
@@ -140,6 +143,15 @@ def weno_right(order: int, in8, eps: float = 1e-6):
     out = np.zeros(2)
     lib().orc_weno_right(order, _p(x), eps, _p(out))
     return out[0], out[1]
+
+
+def tan_weno(q5, g: int, der: int = 0, eps: float = 1e-6):
+    """Tangential WENO-Z (reading R9's variant) of 5 segment averages at Gauss point g:
+    (value or d/ds at s_g, the rule's 3 linear weights)."""
+    q = np.ascontiguousarray(np.asarray(q5, dtype=np.float64))
+    d = np.zeros(3)
+    v = lib().orc_tan_weno(_p(q), int(g), int(der), float(eps), _p(d))
+    return v, d
 
 
 def tangential_weights():
@@ -220,7 +232,7 @@ class Solver:
                  order: int = 6, recon: int = 0, bc_x: int = 0, bc_y: int = 0,
                  x0: float = 0.0, x1: float = 1.0, y0: float = 0.0, y1: float = 1.0,
                  weno_eps: float = 1e-6, tau_mode: int = 0, flux_mode: int = 0,
-                 eq_mode: int = 1, char_mode: int = 0):
+                 eq_mode: int = 1, char_mode: int = 0, tan_mode: int = 0):
         self.nx, self.ny = nx, ny
         self.dim = 2 if ny > 1 else 1
         self.nv = self.dim + 2
@@ -230,6 +242,7 @@ class Solver:
             raise ValueError("invalid oracle parameters")
         lib().orc_set_eq_mode(self._h, int(eq_mode))
         lib().orc_set_char_mode(self._h, int(char_mode))
+        lib().orc_set_tan_mode(self._h, int(tan_mode))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -221,6 +221,13 @@ struct Tables {
   // at the 3 Gauss points
   double tan_w[3][3][5];
   double gauss_s[3], gauss_w[3];
+  // tangential WENO-Z variant of R9: quadratic candidates on the segments {-2,-1,0},
+  // {-1,0,1}, {0,1,2} (coefficients of s^p as functionals of the 5 averages), their value /
+  // d/ds weights at the Gauss points, and the linear weights that recombine them into the
+  // quartic's value / d/ds there
+  double tq[3][3][5];
+  double tq_w[3][2][3][5];   // [g][der][k][m]
+  double tq_d[3][2][3];      // [g][der][k]
 };
 
 Tables build_tables() {
@@ -284,6 +291,37 @@ Tables build_tables() {
           T.tan_w[g][q][m] = s;
         }
   }
+  // Tangential WENO candidates (R9 variant): each quadratic is fixed by the averages over its
+  // three unit segments; the linear weights d solve sum_k d_k p_k^(der)(s_g) = P4^(der)(s_g)
+  // for every data set, i.e. 5 equations (one per average) in 3 unknowns, consistent, solved
+  // through the normal equations.
+  for (int k = 0; k < 3; ++k) {
+    double A[9], B[15];
+    for (int r = 0; r < 3; ++r) {
+      double a = (k + r - 2) - 0.5, b = (k + r - 2) + 0.5;
+      for (int p = 0; p < 3; ++p) A[r * 3 + p] = (ipow(b, p + 1) - ipow(a, p + 1)) / (p + 1);
+      for (int m = 0; m < 5; ++m) B[r * 5 + m] = (m == k + r) ? 1.0 : 0.0;
+    }
+    if (!gauss_solve(3, A, B, 5)) std::abort();
+    for (int p = 0; p < 3; ++p) for (int m = 0; m < 5; ++m) T.tq[k][p][m] = B[p * 5 + m];
+  }
+  for (int g = 0; g < 3; ++g)
+    for (int der = 0; der < 2; ++der) {
+      for (int k = 0; k < 3; ++k)
+        for (int m = 0; m < 5; ++m) {
+          double s = 0.0;
+          for (int p = der; p < 3; ++p) s += (der ? p : 1) * T.tq[k][p][m] * ipow(T.gauss_s[g], p - der);
+          T.tq_w[g][der][k][m] = s;
+        }
+      double N[9] = {0}, r[3] = {0};
+      for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b)
+          for (int m = 0; m < 5; ++m) N[a * 3 + b] += T.tq_w[g][der][a][m] * T.tq_w[g][der][b][m];
+        for (int m = 0; m < 5; ++m) r[a] += T.tq_w[g][der][a][m] * T.tan_w[g][der][m];
+      }
+      if (!gauss_solve(3, N, r, 1)) std::abort();
+      for (int k = 0; k < 3; ++k) T.tq_d[g][der][k] = r[k];
+    }
   return T;
 }
 
@@ -347,6 +385,44 @@ void weno_right(int oi, const double* in, double eps, double* val, double* der) 
   double d;
   weno_left(oi, m, eps, val, &d, nullptr, nullptr);
   *der = -d;
+}
+
+// Tangential WENO-Z at Gauss point g (R9 variant): value (der = 0) or d/ds (der = 1) at s_g
+// of the centre segment from the 5 segment averages q[0..4] (offsets -2..2, unit spacing).
+// Smoothness indicators of the three quadratics by Eq. (smooth-indicator), the WENO-Z weights
+// of Eq. (WENO-Z-w) with the fifth-order reference value |beta_0 - beta_2| of the classical
+// five-point WENO-Z.  Where a linear weight is negative (the value at the centre point:
+// -9/80, 49/40, -9/80) the weights are split into two positive sets and recombined, the
+// treatment of negative linear weights by Shi, Hu and Shu (J. Comput. Phys. 175, 2002), with
+// theta = 3.
+double tan_weno(const double* q, int g, int der, double eps) {
+  const Tables& T = tables();
+  double pv[3], beta[3];
+  for (int k = 0; k < 3; ++k) {
+    double c[8] = {0};
+    for (int p = 0; p < 3; ++p) for (int m = 0; m < 5; ++m) c[p] += T.tq[k][p][m] * q[m];
+    beta[k] = smoothness(c, 2);
+    pv[k] = 0.0;
+    for (int m = 0; m < 5; ++m) pv[k] += T.tq_w[g][der][k][m] * q[m];
+  }
+  const double Z = std::fabs(beta[0] - beta[2]);
+  const double* d = T.tq_d[g][der];
+  auto combine = [&](const double* dd) {
+    double al[3], as = 0.0, out = 0.0;
+    for (int k = 0; k < 3; ++k) { al[k] = dd[k] * (1.0 + Z / (beta[k] + eps)); as += al[k]; }
+    for (int k = 0; k < 3; ++k) out += al[k] / as * pv[k];
+    return out;
+  };
+  if (d[0] >= 0.0 && d[1] >= 0.0 && d[2] >= 0.0) return combine(d);
+  const double theta = 3.0;
+  double gp[3], gm[3], sp = 0.0, sm = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    gp[k] = 0.5 * (d[k] + theta * std::fabs(d[k]));
+    gm[k] = gp[k] - d[k];
+    sp += gp[k]; sm += gm[k];
+  }
+  for (int k = 0; k < 3; ++k) { gp[k] /= sp; gm[k] /= sm; }
+  return sp * combine(gp) - sm * combine(gm);
 }
 
 // ===========================================================================
@@ -665,6 +741,8 @@ void euler_right_eigvecs(int dim, double gamma, const double* W, double* R) {
 struct Solver {
   int nx, ny, dim, nv, order, recon, bcx, bcy;
   int char_mode = 0;   // R8: 0 = characteristic variables at the mean state, 1 = component-wise
+  int tan_mode = 0;    // R9: 0 = tangential quartic for every quantity, 1 = WENO-Z for the
+                       // non-equilibrium states (tan_weno)
   double x0, x1, y0, y1, dx, dy, weno_eps;
   Phys ph;
   std::vector<double> W, Wx, Wy;   // [nv][ny][nx]
@@ -776,6 +854,40 @@ bool normal_recon(const Solver& S, const double in8[4][8], double h, FaceRecon& 
   return true;
 }
 
+// Tangential reconstruction at Gauss point g of a face from the line averages of its five
+// face rows rr[0..4] (rows j-2..j+2; Sec. 3.1 last paragraph, R9); ht = the tangential cell
+// size.  The quartic through the five line averages gives every quantity's value and
+// tangential derivatives (tan_mode 0), or, with tan_mode 1, the equilibrium quantities only,
+// while the initial non-equilibrium states Wl, Wr (value and tangential derivative) and their
+// normal derivatives come from tangential WENO-Z, component-wise.
+void tangential_point(const Solver& S, const FaceRecon* const* rr, int g, double ht, PointIn& pin) {
+  const Tables& T = tables();
+  const int n = S.nv;
+  const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
+  for (int v = 0; v < n; ++v) {
+    for (int t = 0; t < 5; ++t) {
+      const FaceRecon& r = *rr[t];
+      pin.W0[v] += wv[t] * r.W0[v];
+      pin.W0y[v] += wd[t] * r.W0[v] / ht;
+      pin.W0yy[v] += wdd[t] * r.W0[v] / (ht * ht);
+      pin.W0x[v] += wv[t] * r.W0n[v];
+      pin.W0xy[v] += wd[t] * r.W0n[v] / ht;
+      pin.W0xx[v] += wv[t] * r.W0nn[v];
+      pin.Wl[v] += wv[t] * r.Wl[v]; pin.Wly[v] += wd[t] * r.Wl[v] / ht; pin.Wlx[v] += wv[t] * r.Wln[v];
+      pin.Wr[v] += wv[t] * r.Wr[v]; pin.Wry[v] += wd[t] * r.Wr[v] / ht; pin.Wrx[v] += wv[t] * r.Wrn[v];
+    }
+  }
+  if (S.tan_mode != 1 || S.recon != 1) return;
+  for (int v = 0; v < n; ++v) {
+    double ql[5], qln[5], qr[5], qrn[5];
+    for (int t = 0; t < 5; ++t) { ql[t] = rr[t]->Wl[v]; qln[t] = rr[t]->Wln[v]; qr[t] = rr[t]->Wr[v]; qrn[t] = rr[t]->Wrn[v]; }
+    pin.Wl[v] = tan_weno(ql, g, 0, S.weno_eps); pin.Wly[v] = tan_weno(ql, g, 1, S.weno_eps) / ht;
+    pin.Wlx[v] = tan_weno(qln, g, 0, S.weno_eps);
+    pin.Wr[v] = tan_weno(qr, g, 0, S.weno_eps); pin.Wry[v] = tan_weno(qr, g, 1, S.weno_eps) / ht;
+    pin.Wrx[v] = tan_weno(qrn, g, 0, S.weno_eps);
+  }
+}
+
 // Per-face results of one stage, Gauss-averaged over the face.
 struct FaceOut { double F[4], Ft[4], W0[4], Wt[4], Wtt[4]; };
 
@@ -832,20 +944,7 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
           rr[t] = &rx[(size_t)map_index(j - 2 + t, ny, S.bcy) * (nx + 1) + f];
           if (is_mirror(j - 2 + t, ny, S.bcy)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
         }
-        const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
-        for (int v = 0; v < n; ++v) {
-          for (int t = 0; t < 5; ++t) {
-            const FaceRecon& r = *rr[t];
-            pin.W0[v] += wv[t] * r.W0[v];
-            pin.W0y[v] += wd[t] * r.W0[v] / S.dy;
-            pin.W0yy[v] += wdd[t] * r.W0[v] / (S.dy * S.dy);
-            pin.W0x[v] += wv[t] * r.W0n[v];
-            pin.W0xy[v] += wd[t] * r.W0n[v] / S.dy;
-            pin.W0xx[v] += wv[t] * r.W0nn[v];
-            pin.Wl[v] += wv[t] * r.Wl[v]; pin.Wly[v] += wd[t] * r.Wl[v] / S.dy; pin.Wlx[v] += wv[t] * r.Wln[v];
-            pin.Wr[v] += wv[t] * r.Wr[v]; pin.Wry[v] += wd[t] * r.Wr[v] / S.dy; pin.Wrx[v] += wv[t] * r.Wrn[v];
-          }
-        }
+        tangential_point(S, rr, g, S.dy, pin);
       }
       PointOut po;
       if (!gks_point(S.ph, pin, dt, po)) {
@@ -896,19 +995,7 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
         rr[t] = &ry[(size_t)f * nx + map_index(i - 2 + t, nx, S.bcx)];
         if (is_mirror(i - 2 + t, nx, S.bcx)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
       }
-      const double* wv = T.tan_w[g][0]; const double* wd = T.tan_w[g][1]; const double* wdd = T.tan_w[g][2];
-      for (int v = 0; v < n; ++v)
-        for (int t = 0; t < 5; ++t) {
-          const FaceRecon& r = *rr[t];
-          pin.W0[v] += wv[t] * r.W0[v];
-          pin.W0y[v] += wd[t] * r.W0[v] / S.dx;
-          pin.W0yy[v] += wdd[t] * r.W0[v] / (S.dx * S.dx);
-          pin.W0x[v] += wv[t] * r.W0n[v];
-          pin.W0xy[v] += wd[t] * r.W0n[v] / S.dx;
-          pin.W0xx[v] += wv[t] * r.W0nn[v];
-          pin.Wl[v] += wv[t] * r.Wl[v]; pin.Wly[v] += wd[t] * r.Wl[v] / S.dx; pin.Wlx[v] += wv[t] * r.Wln[v];
-          pin.Wr[v] += wv[t] * r.Wr[v]; pin.Wry[v] += wd[t] * r.Wr[v] / S.dx; pin.Wrx[v] += wv[t] * r.Wrn[v];
-        }
+      tangential_point(S, rr, g, S.dx, pin);
       PointOut po;
       if (!gks_point(S.ph, pin, dt, po)) {
 #pragma omp critical
@@ -1137,6 +1224,16 @@ void orc_destroy(void* h) { delete static_cast<Solver*>(h); }
 void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; }
 // R8 option: 0 = WENO-Z in characteristic variables (default), 1 = component-wise.
 void orc_set_char_mode(void* h, int m) { static_cast<Solver*>(h)->char_mode = m; }
+// R9 option: 0 = tangential quartic for every face quantity (default), 1 = tangential WENO-Z
+// for the non-equilibrium states (WENO-Z schemes only).
+void orc_set_tan_mode(void* h, int m) { static_cast<Solver*>(h)->tan_mode = m; }
+// Tangential WENO-Z of 5 segment averages at Gauss point g: value (der 0) or d/ds (der 1);
+// linear weights (3) of that rule into d3.
+double orc_tan_weno(const double* q5, int g, int der, double eps, double* d3) {
+  const Tables& T = tables();
+  if (d3) for (int k = 0; k < 3; ++k) d3[k] = T.tq_d[g][der][k];
+  return tan_weno(q5, g, der, eps);
+}
 void orc_set_state(void* h, const double* W, const double* Wx, const double* Wy) {
   Solver* S = static_cast<Solver*>(h);
   std::memcpy(S->W.data(), W, sizeof(double) * S->W.size());

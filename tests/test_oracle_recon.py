@@ -6,6 +6,8 @@ exact polynomial reproduction, and with the modified-wavenumber closed forms (Se
 """
 from fractions import Fraction
 
+import math
+
 import numpy as np
 import pytest
 
@@ -239,3 +241,68 @@ def test_tangential_quartic_exactness_and_gauss_rule():
     for k in range(6):
         exact = ((0.5) ** (k + 1) - (-0.5) ** (k + 1)) / (k + 1)
         assert abs(np.sum(gw * gs ** k) - exact) < 1e-15
+
+
+# --------------------------------------------------------------------------- tangential WENO-Z
+def _avg_poly(offsets, deg, q):
+    """Polynomial (coefficients of s^p) whose averages over the unit segments centred at
+    `offsets` are q (numpy, independent of the oracle)."""
+    A = np.array([[((o + 0.5) ** (p + 1) - (o - 0.5) ** (p + 1)) / (p + 1) for p in range(deg + 1)]
+                  for o in offsets])
+    return np.linalg.solve(A, np.asarray(q, dtype=float))
+
+
+def _eval(c, s, der=0):
+    return np.polyval(np.polyder(c[::-1], der) if der else c[::-1], s)
+
+
+GAUSS = [-0.5 * math.sqrt(0.6), 0.0, 0.5 * math.sqrt(0.6)]
+
+
+@pytest.mark.parametrize("g", [0, 1, 2])
+@pytest.mark.parametrize("der", [0, 1])
+def test_tangential_weno_linear_weights_recombine_the_quartic(g, der):
+    """Variant of reading R9: the linear weights of the three quadratic candidates at a Gauss
+    point give the quartic through the five line averages, for any data (random data, the
+    candidates and the quartic built here with numpy); the value weights at the outer points
+    are positive (126/655 +- 71 sqrt(15)/5240, 403/655), at the centre negative at both ends
+    (-9/80, 49/40, -9/80); the derivative weights are positive."""
+    rng = np.random.default_rng(g + 3 * der)
+    _, d = oracle.tan_weno([0.0] * 5, g, der)
+    for _ in range(5):
+        q = rng.standard_normal(5)
+        P4 = _avg_poly([-2, -1, 0, 1, 2], 4, q)
+        cands = [_avg_poly(offs, 2, q[k:k + 3]) for k, offs in enumerate(([-2, -1, 0], [-1, 0, 1], [0, 1, 2]))]
+        lhs = sum(d[k] * _eval(cands[k], GAUSS[g], der) for k in range(3))
+        assert abs(lhs - _eval(P4, GAUSS[g], der)) < 1e-13 * (1 + np.abs(q).max())
+    if der == 0 and g != 1:
+        r = 71 * math.sqrt(15) / 5240
+        want = [126 / 655 + r, 403 / 655, 126 / 655 - r]
+        np.testing.assert_allclose(d, want if g == 0 else want[::-1], rtol=1e-12)
+    elif der == 0:
+        np.testing.assert_allclose(d, [-9 / 80, 49 / 40, -9 / 80], rtol=1e-12)
+    else:
+        assert (d > 0).all()
+
+
+@pytest.mark.parametrize("g", [0, 1, 2])
+def test_tangential_weno_on_smooth_and_step_data(g):
+    """Smooth data: the WENO-Z value and derivative approach the quartic's (the candidates'
+    weights tend to the linear ones) faster than the quartic's own error shrinks; step data:
+    the outer-point values stay within the data range (no overshoot), where the quartic
+    overshoots."""
+    errs = []
+    for h in (0.8, 0.4, 0.2):
+        # averages of 2 + sin(h s + 0.7) (no symmetry about the centre, so the weights move)
+        q = [(math.cos(h * (o - 0.5) + 0.7) - math.cos(h * (o + 0.5) + 0.7)) / h + 2.0 for o in range(-2, 3)]
+        P4 = _avg_poly([-2, -1, 0, 1, 2], 4, q)
+        v, _ = oracle.tan_weno(q, g, 0)
+        dv, _ = oracle.tan_weno(q, g, 1)
+        errs.append(max(abs(v - _eval(P4, GAUSS[g])), abs(dv - _eval(P4, GAUSS[g], 1)) / h))
+    assert errs[0] > 4 * errs[1] > 16 * errs[2] and errs[2] < 1e-5, errs
+    step = [1.0, 1.0, 1.0, 0.0, 0.0]
+    P4 = _avg_poly([-2, -1, 0, 1, 2], 4, step)
+    v, _ = oracle.tan_weno(step, g, 0)
+    if g != 1:
+        assert -1e-6 <= v <= 1.0 + 1e-6
+    assert _eval(P4, GAUSS[2]) > 1.0 + 1e-3 or _eval(P4, GAUSS[0]) > 1.0 + 1e-3
