@@ -1,13 +1,21 @@
 """Benchmark of the GB300 compact gas-kinetic scheme (one JSON line on rank 0).
 
-Workload: 2D Euler isentropic vortex (strength 5, gamma 1.4) on periodic [0,10]^2, 2048^2
-cells, 8th-order compact linear reconstruction, fixed dt = CFL 0.3.  A step is one full
-two-stage MSMD step (both face sweeps and both updates, twice).  Both forms run on the same
-input: the FP32-bulk form (the headline value) and the plain FP64 form; each reports its
-L1 density error against the exact (translated) solution at the end of its run.
+Headline workload: 2D Euler isentropic vortex (strength 5, gamma 1.4) on periodic [0,10]^2,
+2048^2 cells, 8th-order compact linear reconstruction, fixed dt = CFL 0.3.  A step is one
+full two-stage MSMD step (both face sweeps and both updates, twice).  Both forms run on the
+same input: the FP32-bulk form (the headline value) and the plain FP64 form; each reports its
+L1 density error against the exact (translated) solution at the end of its run.  Each form
+is timed twice over the same number of steps: as the CUDA-graph replay that gks_steps runs
+(the value) and as plain launches between per-launch CUDA events (gks_steps_timed: the
+per-kernel times and the roofline of the longest launch).
 Metric: cell-updates/s = cells * steps / seconds (whole job: summed over ranks).
 
+The default line also carries two sub-objects measured in the same run: "shear", the 4096^2
+Navier-Stokes double shear layer (8th-order WENO-Z, both forms), and "batch", 512 mixed
+independent problems in one persistent launch per step (FP32-bulk, autotuned tiles).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference] [--n 2048]
+                  [--workload vortex|shear|batch] [--no-sub]
 
 --impl reference times the FP64 CPU oracle (the plain implementation the tests check the
 GPU against) on the host cores, on bounded windows of the same workload.
@@ -49,18 +57,30 @@ CFL = 0.3
 # capture fits in L2.  winstr: executed warp-instructions per 32 units (same captures), for
 # the instruction-issue rate the sweeps are limited by (reported beside the roofline).
 KERNEL_MODEL = {
-    ("fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2, "winstr": 7353},
-    ("fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
-    ("fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
-    ("fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
-    ("fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0, "winstr": 2459},
-    ("fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0, "winstr": 2220},
-    ("fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0, "traffic": 249.0,
-                                "winstr": 408},
-    ("fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0, "winstr": 1924},
-    ("fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0, "winstr": 1717},
-    ("fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0, "traffic": 343.0,
-                                "winstr": 656},
+    ("linear_euler", "fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2, "winstr": 7353},
+    ("linear_euler", "fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
+    ("linear_euler", "fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
+    ("linear_euler", "fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
+    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0,
+                                                 "winstr": 2459},
+    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0,
+                                                 "winstr": 2220},
+    ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
+                                                "traffic": 249.0, "winstr": 408},
+    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0,
+                                                 "winstr": 1924},
+    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0,
+                                                 "winstr": 1717},
+    ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
+                                                "traffic": 343.0, "winstr": 656},
+    # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
+    # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face from a 1024^2 capture
+    ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 11501.0, "f64": 427.0},
+    ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10185.0, "f64": 427.0},
+    ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 11389.0, "f64": 396.0},
+    ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 10073.0, "f64": 396.0},
+    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0},
+    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0},
 }
 HBM_FALLBACK_GBS = 6800.0
 
@@ -77,13 +97,13 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s GB300 copy bandwidth)"
 
 
-def roofline(form, name, ms, nx, ny, order, peak64, peak32, issue_peak=None):
+def roofline(form, name, ms, nx, ny, order, peak64, peak32, issue_peak=None, path="linear_euler"):
     """Roofline of one launch of kernel `name` taking `ms` milliseconds: the fraction of the
     FP32 and FP64 peaks (probes measured in this run) and of the HBM bandwidth, the largest
     named as the bound, the others listed beside it.  With issue_peak (warp-instructions per
     second the SMs can issue), the launch's instruction-issue rate is listed beside them too
     (executed instructions are not algorithmic work, so it is never the headline bound)."""
-    m = KERNEL_MODEL.get((form, name)) if order == 8 else None
+    m = KERNEL_MODEL.get((path, form, name)) if order == 8 else None
     if m is None:
         return {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": name}
@@ -124,7 +144,7 @@ def roofline(form, name, ms, nx, ny, order, peak64, peak32, issue_peak=None):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
     ap.add_argument("--n", type=int, default=None,
@@ -139,6 +159,12 @@ def parse():
                          "shear: the Navier-Stokes double shear layer (8th-order WENO-Z, 4096^2); "
                          "batch: the mixed batch of 512 problems (persistent launch, FP32-bulk)")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-sub", action="store_true",
+                    help="headline workload only (no shear / batch sub-objects in the line)")
+    ap.add_argument("--shear-n", type=int, default=4096)
+    ap.add_argument("--shear-steps", type=int, default=9,
+                    help="timed steps of the shear sub-object (FP32-bulk; the FP64 form a third)")
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -379,32 +405,27 @@ def _build_spec(spec):
     return inputs.build_problem(spec)
 
 
-def run_batch(args, ws, rank, local):
+def batch_measure(args, ws, rank, local, dist, steps):
     """Mixed batch: 1D Riemann problems (N log-uniform in [100, 20000], WENO-Z) and 2D
     vortices (side log-uniform in [64, 1024], linear), orders 6/8 from the seed; one
-    persistent launch per step, tile shape chosen by the autotuner.
+    persistent launch per step, tile shape chosen by the autotuner.  Returns the measured
+    record (value, ms per step, clocks, configuration and autotuner table).
 
     Some of the random Riemann problems turn non-physical under the scheme within a few steps
     (no limiter; the same happens in the oracle).  The workload is first run untimed for the
-    warm-up + timed step count; problems flagged there are dropped (listed in the JSON line)
+    warm-up + timed step count; problems flagged there are dropped (listed in the record)
     and the batch is rebuilt from the rest, so that every timed cell-update is a real one."""
     import multiprocessing as mp
     from paper_1901_00261_gb300 import inputs
     specs = inputs.batch_specs(args.batch_count, seed=rank)
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:   # before any GPU call
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         states = pool.map(_build_spec, specs, chunksize=4)
-    import numpy as np
     import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     from paper_1901_00261_gb300 import gks
     stream = torch.cuda.Stream()     # the batch runs on this stream; the events are recorded on it
     B = gks.Batch(states, stream=stream.cuda_stream)
     dts = CFL / B.max_wavespeed()
-    B.steps(dts, args.warmup + args.steps)
+    B.steps(dts, args.warmup + steps)
     bad = [int(i) for i in np.nonzero(B.problem_status() != gks.GKS_OK)[0]]
     B.close()
     keep = [i for i in range(len(states)) if i not in set(bad)]
@@ -421,36 +442,137 @@ def run_batch(args, ws, rank, local):
         dist.barrier()
     with ClockSampler(local) as clk:
         t0.record(stream)
-        B.steps(dts, args.steps)
+        B.steps(dts, steps)
         t1.record(stream)
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     B.sync()      # raises if any kept problem failed inside the timed region
     cells = sum(st.nx * st.ny for st in states)
-    value, ms = job_throughput(cells, t0.elapsed_time(t1), args.steps, dist, "cuda")
-    if rank == 0:
-        fpt, bps = B.config()
-        line = {"metric": "cell-updates/s (batched mixed problems, FP32-bulk, persistent launch)",
-                "value": value, "unit": UNIT, "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32-bulk (f64 time coefficients and accumulation)", "data": "synthetic",
-                "config": {"workload": f"batch_{args.batch_count}_mixed", "problems": len(states),
-                           "cells": cells,
-                           "problems_1d": sum(1 for st in states if st.ny == 1),
-                           "problems_2d": sum(1 for st in states if st.ny > 1),
-                           "dropped_nonphysical": [dict(index=i, n=specs[i].n, order=specs[i].order,
-                                                        left=specs[i].left, right=specs[i].right)
-                                                   for i in bad],
-                           "faces_per_thread": fpt, "blocks_per_sm": bps,
-                           "l2": "inputs larger than L2"},
-                "gpu_launches": args.steps, "clocks": clk.summary(),
-                "autotune": report.strip().splitlines()}
-        print(json.dumps(line), flush=True)
+    value, ms = job_throughput(cells, t0.elapsed_time(t1), steps, dist, "cuda")
+    fpt, bps = B.config()
     B.close()
+    return {"metric": "cell-updates/s (batched mixed problems, FP32-bulk, persistent launch)",
+            "value": value, "unit": UNIT, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms / steps,
+            "dtype": "f32-bulk (f64 time coefficients and accumulation)",
+            "config": {"workload": f"batch_{args.batch_count}_mixed", "problems": len(states),
+                       "cells": cells,
+                       "problems_1d": sum(1 for st in states if st.ny == 1),
+                       "problems_2d": sum(1 for st in states if st.ny > 1),
+                       "dropped_nonphysical": [dict(index=i, n=specs[i].n, order=specs[i].order,
+                                                    left=specs[i].left, right=specs[i].right)
+                                               for i in bad],
+                       "faces_per_thread": fpt, "blocks_per_sm": bps,
+                       "l2": "inputs larger than L2"},
+            "gpu_launches": steps, "clocks": clk.summary(),
+            "autotune": report.strip().splitlines()}
+
+
+def run_batch(args, ws, rank, local):
+    """--workload batch: the batch record as the JSON line of its own."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = batch_measure(args, ws, rank, local, dist, args.steps)
+    if rank == 0:
+        line = dict(r)
+        line.update({"n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                     "data": "synthetic"})
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_form(st, form, steps, warmup, stream, local, dist, peaks, path, order, want_acc):
+    """One form of one solver workload: graph-replayed steps (the value), then the same number
+    of plain-launch steps between per-launch CUDA events (per-kernel times, roofline)."""
+    import torch
+    from paper_1901_00261_gb300 import gks, inputs
+    prec = gks.PREC_FP32_BULK if form == "fp32" else gks.PREC_FP64
+    ncell = st.nx * st.ny
+    G = gks.Solver.from_state(st, stream=stream.cuda_stream, precision=prec)
+    dt = CFL / G.max_wavespeed()
+    nl = G.launches_per_step()
+    G.steps(dt, warmup)
+    G.sync()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        G.steps(dt, steps)               # the captured two-stage step, replayed
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    G.sync()
+    value, ms = job_throughput(ncell, ev[0].elapsed_time(ev[1]), steps, dist, "cuda")
+    with ClockSampler(local) as clk2:
+        ev[2].record(stream)
+        kernel_ms = G.steps_timed(dt, steps)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    G.sync()
+    value_plain, ms_plain = job_throughput(ncell, ev[2].elapsed_time(ev[3]), steps, dist, "cuda")
+    per_launch = kernel_ms / steps
+    slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
+                  "x_faces_stage2", "y_faces_stage2", "update_stage2"]
+    k_dom = int(np.argmax(per_launch))
+    csum = clk.summary()
+    issue_peak = None
+    try:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = clk2.summary().get("sm_mhz") or csum.get("sm_mhz") or 2070.0
+        issue_peak = 4.0 * sms * mhz * 1e6
+    except Exception:
+        issue_peak = None
+    roof = roofline(form, slot_names[k_dom], float(per_launch[k_dom]), st.nx, st.ny, order,
+                    peaks["fp64"], peaks["fp32"], issue_peak, path=path)
+    r = {"value": value, "ms_per_step": ms / steps, "steps": steps, "gpu_launches": nl * steps,
+         "api": "gks_steps (CUDA graph of the two-stage step, replayed)",
+         "plain_launches": {"value": value_plain, "ms_per_step": ms_plain / steps,
+                            "api": "gks_steps_timed (plain launches, CUDA events around each)",
+                            "clocks": clk2.summary()},
+         "roofline": roof, "clocks": csum,
+         "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}
+    T = dt * (warmup + 2 * steps)
+    r["t_end"] = T
+    W = None
+    if want_acc:
+        W, _, _ = G.get_state()
+        if path == "linear_euler":
+            ex = inputs.vortex_exact_avg(st.nx, T)
+            r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
+            r["linf_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).max())
+        W = W[0]
+    return r, G, dt, W
+
+
+def solver_workload(st, forms, steps, warmup, stream, local, dist, peaks, path, order, rank, no_acc):
+    """Both forms of a single-grid workload; returns {form: record}, the L1 density difference
+    of the two forms at the end, and the solver/dt of the first form."""
+    out, Ws, keep = {}, {}, None
+    for k, form in enumerate(forms):
+        r, G, dt, W = measure_form(st, form, steps[form], warmup, stream, local, dist, peaks, path,
+                                   order, want_acc=(not no_acc and rank == 0))
+        out[form] = r
+        if W is not None:
+            Ws[form] = W
+        if k == 0:
+            keep = (G, dt)
+        else:
+            G.close()
+    diff = None
+    if len(Ws) == 2 and out["fp32"]["t_end"] == out["fp64"]["t_end"]:
+        diff = float(np.abs(Ws["fp32"] - Ws["fp64"]).mean())
+    return out, diff, keep
 
 
 def main():
@@ -474,78 +596,30 @@ def main():
         torch.cuda.set_device(0)
     from paper_1901_00261_gb300 import gks, inputs
 
-    if args.workload == "shear":
+    shear = args.workload == "shear"
+    if shear:
         st = inputs.shear_layer_2d(args.n, order=args.order)
     else:
         st = inputs.isentropic_vortex_2d(args.n, order=args.order, recon=0)
-    stream = torch.cuda.current_stream()
+    path = "wenoz_ns" if shear else "linear_euler"
+    # the solvers run on this stream and the CUDA events are recorded on it (the legacy
+    # default stream would leave the library to create a stream of its own)
+    stream = torch.cuda.Stream()
     ncell = st.nx * st.ny
-    slot_names = ["x_faces_stage1", "y_faces_stage1", "update_stage1",
-                  "x_faces_stage2", "y_faces_stage2", "update_stage2"]
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    peak64 = gks.probe_alu_peak(True)
-    peak32 = gks.probe_alu_peak(False)
+    peaks = {"fp64": gks.probe_alu_peak(True), "fp32": gks.probe_alu_peak(False)}
     forms = {"both": ["fp32", "fp64"], "fp32": ["fp32"], "fp64": ["fp64"]}[args.precision]
-    results = {}
-    for form in forms:
-        prec = gks.PREC_FP32_BULK if form == "fp32" else gks.PREC_FP64
-        G = gks.Solver.from_state(st, stream=stream.cuda_stream, precision=prec)
-        dt = CFL / G.max_wavespeed()
-        nl = G.launches_per_step()
-        G.steps(dt, args.warmup)
-        G.sync()
-        barrier()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            t0.record(stream)
-            kernel_ms = G.steps_timed(dt, args.steps)
-            t1.record(stream)
-            torch.cuda.synchronize()
-        barrier()
-        G.sync()
-        value, ms = job_throughput(ncell, t0.elapsed_time(t1), args.steps, dist, "cuda")
-        per_launch = kernel_ms / args.steps
-        k_dom = int(np.argmax(per_launch))
-        name = slot_names[k_dom]
-        csum = clk.summary()
-        issue_peak = None
-        try:
-            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-            mhz = csum.get("sm_mhz") or 2070.0
-            issue_peak = 4.0 * sms * mhz * 1e6
-        except Exception:
-            issue_peak = None
-        roof = roofline(form, name, float(per_launch[k_dom]), st.nx, st.ny, args.order, peak64, peak32,
-                        issue_peak)
-        r = {"value": value, "ms_per_step": ms / args.steps,
-             "gpu_launches": nl * args.steps, "roofline": roof, "clocks": csum,
-             "kernel_ms_per_launch": {n: float(v) for n, v in zip(slot_names, per_launch)}}
-        if not args.no_acc and rank == 0:
-            T = dt * (args.warmup + args.steps)
-            W, _, _ = G.get_state()
-            if args.workload == "vortex":
-                ex = inputs.vortex_exact_avg(args.n, T)
-                r["l1_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).mean())
-                r["linf_rho_vs_exact"] = float(np.abs(W[0] - ex[0]).max())
-            r["t_end"] = T
-            results.setdefault("_W", {})[form] = W[0]
-        results[form] = r
-        results.setdefault("_solver", {})[form] = (G, dt)
-
+    steps = {"fp32": args.steps, "fp64": args.steps if not shear else max(1, args.steps // 4)}
+    results, diff, (G, dt) = solver_workload(st, forms, steps, args.warmup, stream, local, dist, peaks,
+                                             path, args.order, rank, args.no_acc)
     head = forms[0]
-    G, dt = results["_solver"][head]
     # end to end through the public API with host buffers: per step, H2D of the state from
     # pinned memory, one step, D2H of the resulting state into pinned memory.  Headline: the
     # pipelined call (gks_step_host_async: copy-in, step and copy-out of consecutive steps
     # overlap); beside it the same work as set_state + step + get_state, one after another.
     e2e = None
     if not args.no_e2e:
+        e_steps = min(args.steps, 50)
         Wp = torch.from_numpy(st.W).pin_memory().numpy()
         Wxp = torch.from_numpy(st.Wx).pin_memory().numpy()
         Wyp = torch.from_numpy(st.Wy).pin_memory().numpy()
@@ -555,10 +629,11 @@ def main():
         for k in range(3):
             G.step_host_async(ins, outs[k], dt)
         G.sync()
-        barrier()
+        if dist is not None:
+            dist.barrier()
         torch.cuda.synchronize()
         tw = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(e_steps):
             G.step_host_async(ins, outs[k % 3], dt)
         G.sync()
         el = time.perf_counter() - tw
@@ -567,7 +642,7 @@ def main():
         o = outs[0]
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e_steps):
             G.set_state(Wp, Wxp, Wyp)
             G.step(dt)
             rc = L.gks_get_state(G._h, ptr(o[0]), ptr(o[1]), ptr(o[2]))
@@ -575,13 +650,14 @@ def main():
         torch.cuda.synchronize()
         el_serial = time.perf_counter() - ts
         bytes_state = 3 * st.W.nbytes
-        e2e = {"value": ncell * args.steps * ws / el, "unit": UNIT,
+        e2e = {"value": ncell * e_steps * ws / el, "unit": UNIT, "steps": e_steps,
                "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
                "api": "gks_step_host_async (pipelined), then gks_sync",
-               "serial": {"value": ncell * args.steps * ws / el_serial,
+               "serial": {"value": ncell * e_steps * ws / el_serial,
                           "api": "gks_set_state + gks_step + gks_get_state per step"},
                "copy_gbs": pinned_copy_gbs(st.W.size * 3)}
 
+    line = None
     if rank == 0:
         h = results[head]
         line = {"metric": metric_of(args), "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -591,14 +667,11 @@ def main():
                 "data": "synthetic", "config": workload_config(args), "e2e": e2e,
                 "gpu_launches": h["gpu_launches"], "roofline": h["roofline"], "clocks": h["clocks"],
                 "kernel_ms_per_launch": h["kernel_ms_per_launch"],
-                "alu_peaks_tflops": {"fp64": peak64 / 1e12, "fp32": peak32 / 1e12}}
+                "alu_peaks_tflops": {"fp64": peaks["fp64"] / 1e12, "fp32": peaks["fp32"] / 1e12}}
         for form in forms:
-            r = results[form]
-            line[form] = {k: r[k] for k in ("value", "ms_per_step", "roofline", "l1_rho_vs_exact",
-                                            "linf_rho_vs_exact", "t_end", "kernel_ms_per_launch") if k in r}
-        if "_W" in results and len(results["_W"]) == 2:
-            a, b = results["_W"]["fp32"], results["_W"]["fp64"]
-            line["fp32_vs_fp64_l1_rho"] = float(np.abs(a - b).mean())
+            line[form] = results[form]
+        if diff is not None:
+            line["fp32_vs_fp64_l1_rho"] = diff
         if not args.no_cpu and ws == 1:
             keep = {}
             line["cpu_baseline"] = cpu_baseline(st, dt, keep=keep)
@@ -607,9 +680,28 @@ def main():
             except Exception as e:  # an auxiliary figure: never lose the line over it
                 line["cpu_baseline"]["single_thread"] = {"unavailable": f"{type(e).__name__}: {e}"}
             line["vs_oracle"] = vs_oracle(keep, dt, forms)
+    G.close()
+
+    # the other two workloads, as sub-objects of the same line
+    if not args.no_sub and not shear:
+        sh = inputs.shear_layer_2d(args.shear_n, order=8)
+        sres, sdiff, (SG, _) = solver_workload(
+            sh, ["fp32", "fp64"], {"fp32": args.shear_steps, "fp64": max(1, args.shear_steps // 3)},
+            args.warmup, stream, local, dist, peaks, "wenoz_ns", 8, rank, True)
+        SG.close()
+        if line is not None:
+            line["shear"] = {"metric": METRIC_SHEAR, "unit": UNIT,
+                             "config": {"workload": f"shear_layer_2d_ns_{args.shear_n}x{args.shear_n}",
+                                        "cells": args.shear_n ** 2, "order": 8, "recon": "wenoz",
+                                        "mu": 1e-4, "Pr": 0.72, "cfl": CFL, "domain": "periodic [0,1]^2",
+                                        "l2_policy": "inputs exceed L2"},
+                             "value": sres["fp32"]["value"], "ms_per_step": sres["fp32"]["ms_per_step"],
+                             "fp32": sres["fp32"], "fp64": sres["fp64"]}
+        bres = batch_measure(args, ws, rank, local, dist, args.batch_steps)
+        if line is not None:
+            line["batch"] = bres
+    if line is not None:
         print(json.dumps(line), flush=True)
-    for form in forms:
-        results["_solver"][form][0].close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -73,27 +73,44 @@ typedef struct gks_opts {
                               for mu = 0, plus the pressure-jump term of the WENO-Z states),
                               i.e. the same tau in the bracket and the exponentials */
   void* stream;            /* cudaStream_t to run on; NULL: the library creates one */
+  int tan_mode;            /* 2D with GKS_RECON_WENOZ, reconstruction along the face (Sec. 3.1,
+                              last paragraph): 0 (default) the quartic through five face
+                              line-averages for every quantity; 1 the quartic for the
+                              equilibrium quantities and five-point WENO-Z at the Gauss points
+                              for the initial non-equilibrium states (their values, tangential
+                              and normal derivatives), as Sec. 3.3 carried across the face:
+                              keeps a discontinuity aligned with the grid physical */
 } gks_opts;
 
 /* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-6,
- * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL. */
+ * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL, tan_mode 0. */
 void gks_default_opts(gks_opts* o);
 
-/* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio;
- * mu >= 0 the dynamic viscosity (0: Euler equations); Pr > 0 the Prandtl number (heat
- * flux of the Chapman-Enskog terms scaled by 1/Pr); order 6 or 8; recon GKS_RECON_*.
- * Requires nx >= 5 and (2D) ny >= 5.  opts may be NULL (defaults).  Returns NULL on
- * error (see gks_last_error). */
+/* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio
+ * of the BGK gas, with K = (4 - 2 gamma)/(gamma - 1) internal degrees of freedom in 2D
+ * (Sec. 2.1) and (3 - gamma)/(gamma - 1) in 1D; mu >= 0 the dynamic viscosity, which sets
+ * the physical collision time tau = mu/p of Sec. 4 (0: Euler equations); Pr > 0 the
+ * Prandtl number (heat flux of the Chapman-Enskog terms scaled by 1/Pr); order 6 or 8, the
+ * compact linear reconstruction P^5 or P^7 of Sec. 3.1; recon GKS_RECON_LINEAR or
+ * GKS_RECON_WENOZ (compact WENO-Z of Sec. 3.3 for the non-equilibrium states).
+ * Requires nx >= 5 and (2D) ny >= 5, every real parameter finite.  opts may be NULL
+ * (defaults).  Allocates the device state and work buffers.  Returns NULL on error (see
+ * gks_last_error). */
 gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int order, int recon,
                     const gks_opts* opts);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char* gks_last_error(void);
 
-/* Copy a host state into the solver (W, Wx: [nvar][ny][nx]; Wy NULL in 1D). Synchronous. */
+/* Copy a host state into the solver: the cell averages W and the cell-averaged gradients
+ * Wx, Wy that the compact scheme carries per cell (Sec. 1; they are updated by Eq.
+ * Gausian-formula of Sec. 2.2), each [nvar][ny][nx] float64; Wy NULL in 1D.  The caller
+ * keeps ownership of the arrays.  Synchronous; GKS_EINVAL for a NULL W or Wx (or Wy in 2D). */
 int gks_set_state(gks_ctx* ctx, const double* W, const double* Wx, const double* Wy);
 
-/* Copy the solver state to host arrays; synchronises and reports device conditions. */
+/* Copy the solver state (cell averages and cell-averaged gradients, as gks_set_state) to
+ * caller-owned host arrays; synchronises and reports device conditions (GKS_ENONPHYSICAL
+ * after a non-physical interface state, the arrays still filled). */
 int gks_get_state(gks_ctx* ctx, double* W, double* Wx, double* Wy);
 
 /* Same with device pointers (device-to-device copies, ordered on the context stream;
@@ -107,7 +124,10 @@ int gks_step(gks_ctx* ctx, double dt);
 /* Advance nsteps >= 0 steps of size dt (asynchronous). */
 int gks_steps(gks_ctx* ctx, double dt, int nsteps);
 
-/* max over cells of (|U| + c)/dx (+ (|V| + c)/dy in 2D); dt = CFL / *out.  Synchronises. */
+/* max over cells of (|U| + c)/dx (+ (|V| + c)/dy in 2D), c = sqrt(gamma p/rho) of the cell
+ * averages: the signal speed of the CFL condition of Sec. 4, dt = CFL / *out.  *out is a
+ * caller-owned host double.  Synchronises; GKS_ENONPHYSICAL if a cell has rho <= 0 or
+ * p <= 0. */
 int gks_max_wavespeed(gks_ctx* ctx, double* out);
 
 /* Pipelined step from host memory to host memory, for a stream of independent steps (an
@@ -155,6 +175,13 @@ int gks_probe_alu_peak(int fp64, double* flops_per_s);
  * b0 = 4 (E0(dt) - 2 E0(dt/2))/dt^2, b1 = 4 (E1(dt) - 2 E1(dt/2))/dt^2.  Synchronous;
  * GKS_EINVAL for a NULL array, n < 0, dt or a theta not finite and > 0. */
 int gks_probe_time_coefs(const double* theta, int n, double dt, double* out);
+
+/* Test probe of the FP64 reciprocal that the single-precision sweeps use for their FP64
+ * reference flux (not part of the method): for host x[i] (n >= 0 entries, each positive,
+ * normal and within the float range), out[i] (host) = the device's 1/x[i], formed from a
+ * single-precision reciprocal refined by two Newton-Raphson steps in FP64.  Synchronous;
+ * GKS_EINVAL for a NULL array or n < 0. */
+int gks_probe_rcp64(const double* x, int n, double* out);
 
 /* Release everything the context owns.  NULL is ignored. */
 void gks_destroy(gks_ctx* ctx);
@@ -229,7 +256,11 @@ void gks_batch_destroy(gks_batch* b);
  * library holds it until the process exits.  Larger nx is rejected with GKS_EINVAL.
  * The call allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
  * The first call on a device looks up the array's device address on that device; make
- * that first call before any stream capture.  Every call shares the one array and the
+ * that first call before any stream capture.  With lazy module loading
+ * (CUDA_MODULE_LOADING=LAZY) the driver places the array in device memory when the
+ * library's module is first loaded on a device, which can be that first call: callers that
+ * must not allocate after start-up make the first call during start-up.  gamma, mu, Pr,
+ * x0, x1 and dt must be finite.  Every call shares the one array and the
  * status word it clears at its start: calls that overlap on the GPU (other streams or
  * threads) race.  Runs on `stream` (NULL: the legacy default stream) and synchronises it
  * before returning; returns GKS_OK, GKS_EINVAL, GKS_ECUDA or GKS_ENONPHYSICAL, with the

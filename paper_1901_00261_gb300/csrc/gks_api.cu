@@ -207,6 +207,7 @@ void gks_default_opts(gks_opts* o) {
   o->eps_tau = 0.01; o->C_tau = 1.0;
   o->use_graph = 1;
   o->tau_mode = 0;
+  o->tan_mode = 0;
   o->stream = nullptr;
 }
 
@@ -229,6 +230,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_FP32_BULK) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
   if (o.tau_mode != 0 && o.tau_mode != 1) { fail(GKS_EINVAL, "tau_mode must be 0 or 1%s"); return nullptr; }
+  if (o.tan_mode != 0 && o.tan_mode != 1) { fail(GKS_EINVAL, "tan_mode must be 0 or 1%s"); return nullptr; }
 
   gks_ctx* c = new (std::nothrow) gks_ctx();
   if (!c) { fail(GKS_ENOMEM, "host allocation failed%s"); return nullptr; }
@@ -242,6 +244,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   c->P.mu = mu; c->P.Pr = Pr;
   c->P.eps_tau = o.eps_tau; c->P.C_tau = o.C_tau; c->P.weno_eps = o.weno_eps;
   c->P.tau_mode = o.tau_mode;
+  c->P.tan_mode = o.tan_mode;
   gks::set_phys_floats(c->P);
 
   cudaError_t e;
@@ -414,6 +417,14 @@ int gks_probe_time_coefs(const double* theta, int n, double dt, double* out) {
   if (n == 0) return GKS_OK;
   cudaError_t e = gks::probe_time_coefs(theta, n, dt, out);
   if (e != cudaSuccess) return cuda_fail(e, "time coefficient probe");
+  return GKS_OK;
+}
+
+int gks_probe_rcp64(const double* x, int n, double* out) {
+  if (!x || !out || n < 0) return fail(GKS_EINVAL, "NULL argument or n < 0%s");
+  if (n == 0) return GKS_OK;
+  cudaError_t e = gks::probe_rcp64(x, n, out);
+  if (e != cudaSuccess) return cuda_fail(e, "reciprocal probe");
   return GKS_OK;
 }
 

@@ -334,12 +334,13 @@ __device__ __forceinline__ void gcol0(const Gm<R, DIM>& G, R s, R* out, bool acc
 struct TimeCoef { double a0, a1, b0, b1; };
 
 // Taylor coefficients of 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x) for
-// phi(y) = 1 - e^{-y}(1 + y) = sum_{k>=2} (-1)^k (k-1) y^k / k!, k = 2..21, formed at compile
-// time.  The series is used for x < 1/2, where the first omitted term is below 1e-19 of the
-// terms' magnitude |4 phi(x)| + |phi(2x)| (resp. |phi(2x)| + |2 phi(x)|); from x = 1/2 on, the
-// closed form loses at most a few ulp of that magnitude to cancellation (1e-15 measured
+// phi(y) = 1 - e^{-y}(1 + y) = sum_{k>=2} (-1)^k (k-1) y^k / k!, k = 2..21, and of
+// S(x) = 1 - e^{-x} = sum_{k>=1} (-1)^(k+1) x^k / k!, formed at compile time.  The series are
+// used for x < 1/2, where the first omitted term is below 1e-19 of the terms' magnitude
+// |4 phi(x)| + |phi(2x)| (resp. |phi(2x)| + |2 phi(x)|; for S, of S itself); from x = 1/2 on,
+// the closed form loses at most a few ulp of that magnitude to cancellation (1e-15 measured
 // against an 80-digit evaluation; at x -> 1 the series would leave 6e-14).
-struct PhiSeries { double a[22], b[22]; };
+struct PhiSeries { double a[22], b[22], s[22]; };
 __host__ __device__ constexpr PhiSeries make_phi_series() {
   PhiSeries c{};
   double fact = 1.0, p2 = 1.0;
@@ -348,6 +349,7 @@ __host__ __device__ constexpr PhiSeries make_phi_series() {
     const double sg = (k & 1) ? -1.0 : 1.0;
     c.a[k] = k >= 2 ? sg * (k - 1) * (4.0 - p2) / fact : 0.0;
     c.b[k] = k >= 2 ? sg * (k - 1) * (p2 - 2.0) / fact : 0.0;
+    c.s[k] = k >= 1 ? -sg / fact : 0.0;
   }
   return c;
 }
@@ -357,30 +359,34 @@ __host__ __device__ constexpr PhiSeries make_phi_series() {
 // FP64): a0 = theta S (2 + S), b0 = -4 theta S^2 / dt, a1 = theta^2 dt pa, b1 = 4 theta^2 pb.
 __device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt) {
   TimeCoef T;
-  // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
-  double S = x > 40.0 ? 1.0 : -expm1(-x);
-  double idt = 1.0 / dt;
-  T.a0 = theta * S * (2.0 + S);
-  T.b0 = -4.0 * theta * S * S * idt;
+  double S;        // 1 - e^{-x}
   double pa, pb;   // 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x), phi(y) = 1 - e^{-y}(1+y)
   if (x < 0.5) {
-    // the series, by Horner's rule in x (x^2 factored out)
+    // the three series, by Horner's rule in x in lockstep (x^2, resp. x, factored out)
     constexpr PhiSeries C = make_phi_series();
-    double qa = C.a[21], qb = C.b[21];
+    double qa = C.a[21], qb = C.b[21], qs = C.s[21];
 #pragma unroll
     for (int k = 20; k >= 2; --k) {
       qa = fma(qa, x, C.a[k]);
       qb = fma(qb, x, C.b[k]);
+      qs = fma(qs, x, C.s[k]);
     }
+    qs = fma(qs, x, C.s[1]);
     const double x2 = x * x;
     pa = qa * x2;
     pb = qb * x2;
+    S = qs * x;
   } else {
+    // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
+    S = x > 40.0 ? 1.0 : -expm1(-x);
     double e = 1.0 - S;   // e^{-x}
     double e2 = e * e;
     pa = 3.0 - 4.0 * e * (1.0 + x) + e2 * (1.0 + 2.0 * x);
     pb = -1.0 + 2.0 * e * (1.0 + x) - e2 * (1.0 + 2.0 * x);
   }
+  double idt = 1.0 / dt;
+  T.a0 = theta * S * (2.0 + S);
+  T.b0 = -4.0 * theta * S * S * idt;
   const double t2 = theta * theta;
   T.a1 = t2 * pa * dt;
   T.b1 = 4.0 * t2 * pb;
@@ -394,6 +400,8 @@ struct PhysParams {
   double gamma, K, mu, Pr, eps_tau, C_tau, weno_eps;
   float gammaf, Kf;   // single-precision copies of gamma and K (set with set_phys_floats)
   int tau_mode = 0;   // 0: bracket with mu/p (reading R1); 1: bracket with the numerical time
+  int tan_mode = 0;   // 2D WENO-Z: 0 tangential quartic for every face quantity; 1 tangential
+                      // WENO-Z for the non-equilibrium states (tan_weno)
 };
 
 inline void set_phys_floats(PhysParams& P) { P.gammaf = (float)P.gamma; P.Kf = (float)P.K; }

@@ -103,7 +103,9 @@ struct Tile {
   static constexpr int NS = SA * SB;
 };
 
-template <int ORDER, bool WENO, bool VISC, int DIR, int STAGE>
+// TANW: tangential WENO-Z for the non-equilibrium states (option tan_mode 1, WENO-Z only),
+// compiled into instantiations of its own.
+template <int ORDER, bool WENO, bool VISC, int DIR, int STAGE, bool TANW = false>
 __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   typedef double R;
   const int N = 4;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   for (int t = 0; t < 5; ++t)
     slot[t] = DIR == 0 ? (threadIdx.y + t) * T::SA + threadIdx.x : threadIdx.y * T::SA + threadIdx.x + t;
   const R it = R(1) / R(a.dtan);
+  const bool tanw = WENO && TANW;
   double F[N] = {0}, Ft[N] = {0}, W0[N] = {0}, Wt[N] = {0}, Wtt[N] = {0};
   bool ok = true;
 #pragma unroll 1
@@ -204,6 +207,19 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
       if (WENO) {
         pin.Wl[v] = l0; pin.Wly[v] = l1 * it; pin.Wlx[v] = ln0;
         pin.Wr[v] = r0; pin.Wry[v] = r1 * it; pin.Wrx[v] = rn0;
+        if (tanw) {   // tangential WENO-Z for the non-equilibrium states (option tan_mode 1)
+          R ql[5], qld[5], qr[5], qrd[5];
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            ql[t] = sm[(3 * N + v) * T::NS + slot[t]]; qld[t] = sm[(4 * N + v) * T::NS + slot[t]];
+            qr[t] = sm[(5 * N + v) * T::NS + slot[t]]; qrd[t] = sm[(6 * N + v) * T::NS + slot[t]];
+          }
+          const R eps = R(a.P.weno_eps);
+          pin.Wl[v] = tan_weno<R, 0>(ql, g, eps); pin.Wly[v] = tan_weno<R, 1>(ql, g, eps) * it;
+          pin.Wlx[v] = tan_weno<R, 0>(qld, g, eps);
+          pin.Wr[v] = tan_weno<R, 0>(qr, g, eps); pin.Wry[v] = tan_weno<R, 1>(qr, g, eps) * it;
+          pin.Wrx[v] = tan_weno<R, 0>(qrd, g, eps);
+        }
       } else {
         pin.Wl[v] = s0; pin.Wly[v] = s1 * it; pin.Wlx[v] = n0;
         pin.Wr[v] = s0; pin.Wry[v] = s1 * it; pin.Wrx[v] = n0;
@@ -247,28 +263,29 @@ cudaError_t launch_faces_1d(const FaceArgs& a, int order, int recon, bool visc, 
   return visc ? launch_1d_t<8, true, true>(a, s) : launch_1d_t<8, true, false>(a, s);
 }
 
-template <int ORDER, bool WENO, bool VISC, int DIR>
-static cudaError_t launch_2d_t(const FaceArgs& a, cudaStream_t s) {
+template <int ORDER, bool WENO, bool VISC, int DIR, bool TANW>
+static cudaError_t launch_2d_tw(const FaceArgs& a, cudaStream_t s) {
   typedef Tile<DIR> T;
   const int NQ = WENO ? 7 : 3;
   size_t shmem = sizeof(double) * NQ * 4 * T::NS;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_kernel<ORDER, WENO, VISC, DIR, 1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(faces_2d_kernel<ORDER, WENO, VISC, DIR, 2>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  const void* fns[2] = {(const void*)faces_2d_kernel<ORDER, WENO, VISC, DIR, 1, TANW>,
+                        (const void*)faces_2d_kernel<ORDER, WENO, VISC, DIR, 2, TANW>};
+  cudaError_t e = smem_limit_per_device(smem_set, fns, 2, (int)shmem);
+  if (e != cudaSuccess) return e;
   dim3 block(TA, TB);
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + 1 + TA - 1) / TA, (a.ny + TB - 1) / TB);
   else grid = dim3((a.nx + TA - 1) / TA, (a.ny + 1 + TB - 1) / TB);
-  if (a.stage == 1) faces_2d_kernel<ORDER, WENO, VISC, DIR, 1><<<grid, block, shmem, s>>>(a);
-  else faces_2d_kernel<ORDER, WENO, VISC, DIR, 2><<<grid, block, shmem, s>>>(a);
+  if (a.stage == 1) faces_2d_kernel<ORDER, WENO, VISC, DIR, 1, TANW><<<grid, block, shmem, s>>>(a);
+  else faces_2d_kernel<ORDER, WENO, VISC, DIR, 2, TANW><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int ORDER, bool WENO, bool VISC, int DIR>
+static cudaError_t launch_2d_t(const FaceArgs& a, cudaStream_t s) {
+  if (WENO && a.P.tan_mode == 1) return launch_2d_tw<ORDER, WENO, VISC, DIR, WENO>(a, s);
+  return launch_2d_tw<ORDER, WENO, VISC, DIR, false>(a, s);
 }
 
 template <int ORDER, bool WENO, bool VISC>

@@ -44,36 +44,41 @@ cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool vi
 #define SWEEP32_FPT 2
 #endif
 
-template <int ORDER, bool WENO, bool VISC, int DIR, bool WALLS>
+template <int ORDER, bool WENO, bool VISC, int DIR, bool WALLS, bool TANW>
 static cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
   const int FPT = SWEEP32_FPT;
   typedef Tile32<DIR, FPT> T;
   const size_t shmem = T::smem_bytes(WENO);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_set{0};
+  const void* fns[2] = {(const void*)faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS, TANW>,
+                        (const void*)faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS, TANW>};
+  cudaError_t e = smem_limit_per_device(smem_set, fns, 2, (int)shmem);
+  if (e != cudaSuccess) return e;
   dim3 block(TA32, TB32);
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + 1 + TA32 - 1) / TA32, (a.ny + T::TB - 1) / T::TB);
   else grid = dim3((a.nx + TA32 - 1) / TA32, (a.ny + 1 + T::TB - 1) / T::TB);
-  if (a.stage == 1) faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS><<<grid, block, shmem, s>>>(a);
-  else faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS><<<grid, block, shmem, s>>>(a);
+  if (a.stage == 1) faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 1, WALLS, TANW><<<grid, block, shmem, s>>>(a);
+  else faces_2d_f32_kernel<ORDER, WENO, VISC, DIR, FPT, 2, WALLS, TANW><<<grid, block, shmem, s>>>(a);
   return cudaGetLastError();
+}
+
+// tan_mode 1 (tangential WENO-Z) selects separate instantiations of the WENO-Z tiles, so that
+// the default tiles carry none of its code or registers
+template <int ORDER, bool WENO, bool VISC, bool WALLS>
+static cudaError_t launch_2d32_tw(const FaceArgs32& a, int dir, cudaStream_t s) {
+  if (WENO && a.P.tan_mode == 1)
+    return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, WALLS, WENO>(a, s)
+                    : launch_2d32_t<ORDER, WENO, VISC, 1, WALLS, WENO>(a, s);
+  return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, WALLS, false>(a, s)
+                  : launch_2d32_t<ORDER, WENO, VISC, 1, WALLS, false>(a, s);
 }
 
 template <int ORDER, bool WENO, bool VISC>
 static cudaError_t launch_2d32_dir(const FaceArgs32& a, int dir, cudaStream_t s) {
   const bool walls = a.bcx == 2 || a.bcy == 2;
-  if (walls)
-    return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, true>(a, s) : launch_2d32_t<ORDER, WENO, VISC, 1, true>(a, s);
-  return dir == 0 ? launch_2d32_t<ORDER, WENO, VISC, 0, false>(a, s) : launch_2d32_t<ORDER, WENO, VISC, 1, false>(a, s);
+  if (walls) return launch_2d32_tw<ORDER, WENO, VISC, true>(a, dir, s);
+  return launch_2d32_tw<ORDER, WENO, VISC, false>(a, dir, s);
 }
 
 cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon, bool visc, cudaStream_t s) {
@@ -83,6 +88,26 @@ cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon
   }
   if (recon == 0) return visc ? launch_2d32_dir<8, false, true>(a, dir, s) : launch_2d32_dir<8, false, false>(a, dir, s);
   return visc ? launch_2d32_dir<8, true, true>(a, dir, s) : launch_2d32_dir<8, true, false>(a, dir, s);
+}
+
+__global__ void rcp64_probe_kernel(const double* x, int n, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = rcp64(x[i]);
+}
+
+// rcp64 of host x[0..n) into host out[0..n); synchronous (test probe).
+cudaError_t probe_rcp64(const double* x, int n, double* out) {
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * (size_t)n * sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    rcp64_probe_kernel<<<(n + 127) / 128, 128>>>(d, n, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e;
 }
 
 cudaError_t launch_update32(const UpdateArgs32& a, int dim, int stage, cudaStream_t s) {

@@ -3,9 +3,31 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "gks_device.cuh"
 
 namespace gks {
+
+// Raise the dynamic shared-memory limit of kernels fns[0..n) to `bytes` on the current
+// device, once per device: function attributes belong to a device, so each device that
+// launches the kernels needs its own setting.  `done` holds one bit per device (devices
+// 64 and above set the attribute on every call).  Setting it twice is harmless, so two host
+// threads that race on the first launch both set it.
+inline cudaError_t smem_limit_per_device(std::atomic<unsigned long long>& done,
+                                         const void* const* fns, int n, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  for (int i = 0; i < n; ++i) {
+    e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  if (bit) done.fetch_or(bit, std::memory_order_release);
+  return cudaSuccess;
+}
 
 // Status bits written by kernels (read back by the host at synchronising calls).
 enum : unsigned int { ST_NONPHYSICAL = 1u, ST_NONFINITE = 2u };
@@ -94,5 +116,8 @@ cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
 cudaError_t launch_set_times(StepTimes* p, double dt, cudaStream_t s);
 cudaError_t probe_fma(int fp64, int iters, double* flops, cudaStream_t s);
 cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out);
+
+// Test probe: the FP32-bulk sweeps' FP64 reciprocal of host x[0..n) into host out.
+cudaError_t probe_rcp64(const double* x, int n, double* out);
 
 }  // namespace gks

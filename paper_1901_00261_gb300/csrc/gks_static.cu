@@ -80,8 +80,9 @@ extern "C" int gks_step_1d_static(const double* W, const double* Wx, double* W_o
   if (order != 6 && order != 8) return sfail(GKS_EINVAL, "order must be 6 or 8");
   if (recon != GKS_RECON_LINEAR && recon != GKS_RECON_WENOZ) return sfail(GKS_EINVAL, "recon must be 0 or 1");
   if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTING) return sfail(GKS_EINVAL, "bc must be 0, 1 or 2");
-  if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return sfail(GKS_EINVAL, "need gamma > 1, mu >= 0, Pr > 0");
-  if (!(x1 > x0)) return sfail(GKS_EINVAL, "empty domain");
+  if (!isfinite(gamma) || !isfinite(mu) || !isfinite(Pr) || !(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0))
+    return sfail(GKS_EINVAL, "need finite gamma > 1, mu >= 0, Pr > 0");
+  if (!isfinite(x0) || !isfinite(x1) || !(x1 > x0)) return sfail(GKS_EINVAL, "domain must be finite and non-empty");
   if (!(dt > 0.0) || !isfinite(dt)) return sfail(GKS_EINVAL, "dt must be finite and > 0");
 
   double* s = nullptr;

@@ -93,6 +93,107 @@ __device__ __constant__ float TWf[3][3][5] = {
       (float)(-1.0 / 20 + GKS_SQ15 / 20)}}};
 __device__ __constant__ float GWf[3] = {(float)(5.0 / 18), (float)(8.0 / 18), (float)(5.0 / 18)};
 
+// Tangential WENO-Z at the Gauss points (option tan_mode = 1: the initial non-equilibrium
+// states across the face, the WENO reconstruction of Sec. 3.3 carried to the tangential
+// direction).  Candidates: the quadratics through the averages of the unit segments
+// {-2,-1,0}, {-1,0,1}, {0,1,2} (q[0..4] at offsets -2..2).  TQV[g][k][j] / TQD[g][k][j]: weight
+// of q[k + j] in candidate k's value / d/ds at Gauss point g (closed forms).  TQLV, TQLD:
+// the linear weights that recombine the candidates into the quartic's value / d/ds at the
+// outer points and the derivative at the centre; the centre value's linear weights
+// (-9/80, 49/40, -9/80) are split into the positive sets TQP (sum 107/40) and TQM (sum 67/40)
+// with theta = 3 (Shi, Hu and Shu, J. Comput. Phys. 175, 2002).
+#define GKS_TQ_TABLES(T)                                                                           \
+  __device__ __constant__ T TQV##_##T[3][3][3] = {                                                \
+      {{T(1.0 / 30 - GKS_SQ15 / 20), T(-1.0 / 15 + GKS_SQ15 / 5), T(31.0 / 30 - 3 * GKS_SQ15 / 20)},   \
+       {T(1.0 / 30 + GKS_SQ15 / 20), T(14.0 / 15), T(1.0 / 30 - GKS_SQ15 / 20)},                   \
+       {T(31.0 / 30 + 3 * GKS_SQ15 / 20), T(-1.0 / 15 - GKS_SQ15 / 5), T(1.0 / 30 + GKS_SQ15 / 20)}},  \
+      {{T(-1.0 / 24), T(1.0 / 12), T(23.0 / 24)},                                                  \
+       {T(-1.0 / 24), T(13.0 / 12), T(-1.0 / 24)},                                                 \
+       {T(23.0 / 24), T(1.0 / 12), T(-1.0 / 24)}},                                                 \
+      {{T(1.0 / 30 + GKS_SQ15 / 20), T(-1.0 / 15 - GKS_SQ15 / 5), T(31.0 / 30 + 3 * GKS_SQ15 / 20)},   \
+       {T(1.0 / 30 - GKS_SQ15 / 20), T(14.0 / 15), T(1.0 / 30 + GKS_SQ15 / 20)},                   \
+       {T(31.0 / 30 - 3 * GKS_SQ15 / 20), T(-1.0 / 15 + GKS_SQ15 / 5), T(1.0 / 30 - GKS_SQ15 / 20)}}}; \
+  __device__ __constant__ T TQD##_##T[3][3][3] = {                                                \
+      {{T(0.5 - GKS_SQ15 / 10), T(-2.0 + GKS_SQ15 / 5), T(1.5 - GKS_SQ15 / 10)},                    \
+       {T(-0.5 - GKS_SQ15 / 10), T(GKS_SQ15 / 5), T(0.5 - GKS_SQ15 / 10)},                           \
+       {T(-1.5 - GKS_SQ15 / 10), T(2.0 + GKS_SQ15 / 5), T(-0.5 - GKS_SQ15 / 10)}},                  \
+      {{T(0.5), T(-2.0), T(1.5)}, {T(-0.5), T(0.0), T(0.5)}, {T(-1.5), T(2.0), T(-0.5)}},           \
+      {{T(0.5 + GKS_SQ15 / 10), T(-2.0 - GKS_SQ15 / 5), T(1.5 + GKS_SQ15 / 10)},                    \
+       {T(-0.5 + GKS_SQ15 / 10), T(-GKS_SQ15 / 5), T(0.5 + GKS_SQ15 / 10)},                          \
+       {T(-1.5 + GKS_SQ15 / 10), T(2.0 - GKS_SQ15 / 5), T(-0.5 + GKS_SQ15 / 10)}}};                 \
+  __device__ __constant__ T TQLV##_##T[3][3] = {                                                  \
+      {T(126.0 / 655 + 71 * GKS_SQ15 / 5240), T(403.0 / 655), T(126.0 / 655 - 71 * GKS_SQ15 / 5240)},   \
+      {T(0), T(0), T(0)},                                                                          \
+      {T(126.0 / 655 - 71 * GKS_SQ15 / 5240), T(403.0 / 655), T(126.0 / 655 + 71 * GKS_SQ15 / 5240)}};  \
+  __device__ __constant__ T TQLD##_##T[3][3] = {                                                  \
+      {T(29.0 / 60 + 7 * GKS_SQ15 / 60), T(1.0 / 30), T(29.0 / 60 - 7 * GKS_SQ15 / 60)},             \
+      {T(5.0 / 24), T(7.0 / 12), T(5.0 / 24)},                                                     \
+      {T(29.0 / 60 - 7 * GKS_SQ15 / 60), T(1.0 / 30), T(29.0 / 60 + 7 * GKS_SQ15 / 60)}};
+GKS_TQ_TABLES(double)
+GKS_TQ_TABLES(float)
+#undef GKS_TQ_TABLES
+
+template <typename R> struct TanWenoTables;
+template <> struct TanWenoTables<double> {
+  __device__ static const double (&V())[3][3][3] { return TQV_double; }
+  __device__ static const double (&D())[3][3][3] { return TQD_double; }
+  __device__ static const double (&LV())[3][3] { return TQLV_double; }
+  __device__ static const double (&LD())[3][3] { return TQLD_double; }
+};
+template <> struct TanWenoTables<float> {
+  __device__ static const float (&V())[3][3][3] { return TQV_float; }
+  __device__ static const float (&D())[3][3][3] { return TQD_float; }
+  __device__ static const float (&LV())[3][3] { return TQLV_float; }
+  __device__ static const float (&LD())[3][3] { return TQLD_float; }
+};
+
+// Smoothness indicators of the three candidates, Eq. (smooth-indicator) on unit segments:
+// 13/12 (second difference)^2 + 1/4 (first-derivative combination)^2 (Jiang and Shu).
+template <typename R>
+__device__ __forceinline__ void tan_weno_beta(const R* q, R* beta) {
+  const R c13 = R(13.0 / 12.0), c4 = R(0.25);
+  R a = q[0] - R(2) * q[1] + q[2], b = q[0] - R(4) * q[1] + R(3) * q[2];
+  beta[0] = c13 * a * a + c4 * b * b;
+  a = q[1] - R(2) * q[2] + q[3]; b = q[1] - q[3];
+  beta[1] = c13 * a * a + c4 * b * b;
+  a = q[2] - R(2) * q[3] + q[4]; b = R(3) * q[2] - R(4) * q[3] + q[4];
+  beta[2] = c13 * a * a + c4 * b * b;
+}
+
+// WENO-Z combination sum_k delta_k p_k of candidate values p[3] with linear weights d[3],
+// Eq. (WENO-Z-w) with the five-point reference value Z = |beta_0 - beta_2|.
+template <typename R>
+__device__ __forceinline__ R tan_weno_combine(const R* p, const R* beta, R Z, R eps, R d0, R d1, R d2) {
+  const R a0 = d0 * (R(1) + Z / (beta[0] + eps));
+  const R a1 = d1 * (R(1) + Z / (beta[1] + eps));
+  const R a2 = d2 * (R(1) + Z / (beta[2] + eps));
+  return (a0 * p[0] + a1 * p[1] + a2 * p[2]) / (a0 + a1 + a2);
+}
+
+// Tangential WENO-Z value (DER = 0) or d/ds (DER = 1) at Gauss point g of the centre segment
+// from the five segment averages q[0..4].
+template <typename R, int DER>
+__device__ __forceinline__ R tan_weno(const R* q, int g, R eps) {
+  typedef TanWenoTables<R> TT;
+  R beta[3], p[3];
+  tan_weno_beta(q, beta);
+  const R Z = fabs(beta[0] - beta[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R(&w)[3] = DER ? TT::D()[g][k] : TT::V()[g][k];
+    p[k] = w[0] * q[k] + w[1] * q[k + 1] + w[2] * q[k + 2];
+  }
+  if (DER || g != 1) {
+    const R(&d)[3] = DER ? TT::LD()[g] : TT::LV()[g];
+    return tan_weno_combine(p, beta, Z, eps, d[0], d[1], d[2]);
+  }
+  // centre value: positive sets (9, 196, 9)/214 and (9, 49, 9)/67, recombined as
+  // 107/40 u+ - 67/40 u-
+  const R up = tan_weno_combine(p, beta, Z, eps, R(9.0 / 214), R(196.0 / 214), R(9.0 / 214));
+  const R um = tan_weno_combine(p, beta, Z, eps, R(9.0 / 67), R(49.0 / 67), R(9.0 / 67));
+  return R(107.0 / 40) * up - R(67.0 / 40) * um;
+}
+
 // ---------------------------------------------------------------------------
 // Normal reconstruction of one face from its 4-cell stencil, in the face's local frame.
 // in[v][0..3] = W_{i-1..i+2}, in[v][4..7] = dx W'_{i-1..i+2}.

@@ -21,8 +21,9 @@
 namespace gks {
 
 // 1/x for a positive normal x within the float range: a single-precision seed refined by
-// two Newton steps r <- r + r (1 - x r) in FP64 (each squares the relative error, from
-// ~2^-23 to below FP64 rounding).  The reference fluxes only; no IEEE rounding guarantee.
+// two Newton-Raphson steps for f(r) = 1/r - x, r <- r + r (1 - x r), in FP64 (each squares
+// the relative error, from ~2^-23 to below FP64 rounding: within a few ulp of 1/x, tested
+// through gks_probe_rcp64).  The reference fluxes only; no IEEE rounding guarantee.
 __device__ __forceinline__ double rcp64(double x) {
   double r = (double)__frcp_rn((float)x);
   double e = fma(-x, r, 1.0);
@@ -251,6 +252,14 @@ __global__ void __launch_bounds__(128) faces_1d_f32_kernel(FaceArgs32 a) {
 // reference (hi, lo) in shared memory; the face's Gauss points use the reference of the
 // face's own row (tangential slot 2), and the other slots' references enter as
 // (hi_t - hi_c) + (lo_t - lo_c).
+// Shared memory of the linear Euler tile is slot-major: slot s owns a row of 20 floats, [q][v]
+// for the 3 reconstructed quantities of the 4 variables, then the reference hi[4] and lo[4],
+// so that one 128-bit shared load brings a quantity of all four variables; 80-byte rows keep
+// every 128-bit access of a warp free of bank conflicts (8 consecutive rows fall in distinct
+// 16-byte bank groups).  The reference-flux differences follow as one float4 per slot.  The
+// WENO-Z / viscous tiles, bound by registers, keep one plane per quantity and variable
+// ([q][v][slot], then the reference hi and lo planes and the flux differences) and read them
+// one variable at a time.
 // ---------------------------------------------------------------------------
 constexpr int TA32 = 32, TB32 = 4;   // threads per block: TA32 x TB32
 
@@ -261,25 +270,31 @@ struct Tile32 {
   static constexpr int SA = DIR == 0 ? TA32 : TA32 + 4;
   static constexpr int SB = DIR == 0 ? TB + 4 : TB;
   static constexpr int NS = SA * SB;
-  // shared memory: NQ reconstructed quantities, the reference (hi, lo) and the reference-flux
-  // difference of the face's two cells, 4 variables each, per slot
-  static constexpr size_t smem_bytes(bool weno) { return sizeof(float) * ((weno ? 7 : 3) + 3) * 4 * NS; }
+  // shared memory: per slot NQ reconstructed quantities and the reference (hi, lo), 4 variables
+  // each, and the reference-flux difference of the face's two cells (the same size in both
+  // layouts)
+  static constexpr size_t smem_bytes(bool weno) { return sizeof(float) * (4 * (weno ? 7 : 3) + 12) * NS; }
 };
 
 // One tile of TA32 x TB32 faces; tid = linear thread index in a block of TA32 * TB32 threads;
 // (bx, by) = tile coordinates (the block indices of the standalone launch); smf = dynamic
-// shared memory of (NQ + 2) * 4 * NS floats.
+// shared memory of Tile32::smem_bytes(WENO) bytes (slot rows, then the slots' reference-flux differences).
 // WALLS: as for sweep1d_f32_face.
-template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1, int STAGE = 0, bool WALLS = false>
+// TANW: tangential WENO-Z for the non-equilibrium states (option tan_mode 1; WENO-Z tiles).
+template <int ORDER, bool WENO, bool VISC, int DIR, bool CG, int FPT = 1, int STAGE = 0, bool WALLS = false,
+          bool TANW = false>
 __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, int by, int tid, float* smf) {
   const int stage = STAGE ? STAGE : a.stage;
   const int N = 4;
   const int NQ = WENO ? 7 : 3;
   typedef Tile32<DIR, FPT> T;
   const int tx = tid % TA32, ty = tid / TA32;
-  float* sref = smf + NQ * N * T::NS;
+  constexpr bool AOS = !(WENO || VISC);        // slot-major layout (linear Euler tile)
+  constexpr int RS = 4 * NQ + 8;               // floats per slot row (slot-major layout)
+  float4* sdfc = reinterpret_cast<float4*>(smf + RS * T::NS);
+  float* sref = smf + NQ * N * T::NS;          // plane layout
   float* sreflo = sref + N * T::NS;
-  float* sdfc = sreflo + N * T::NS;
+  float* sdfcp = sreflo + N * T::NS;
   const double dt = ldd<CG>(a.dtp);
   const long ncell = (long)a.nx * a.ny;
   const long L = N * ncell;
@@ -342,13 +357,22 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 #pragma unroll
       for (int v = 0; v < N; ++v) { ref[v] = 0.f; rlo[v] = 0.f; }
     }
+    if constexpr (AOS) {
+      float4* row = reinterpret_cast<float4*>(smf + RS * s);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
+      for (int q = 0; q < NQ; ++q) row[q] = make_float4(rec[q][0], rec[q][1], rec[q][2], rec[q][3]);
+      row[NQ] = make_float4(ref[0], ref[1], ref[2], ref[3]);
+      row[NQ + 1] = make_float4(rlo[0], rlo[1], rlo[2], rlo[3]);
+      sdfc[s] = make_float4(dfc[0], dfc[1], dfc[2], dfc[3]);
+    } else {
 #pragma unroll
-      for (int v = 0; v < N; ++v) smf[(q * N + v) * T::NS + s] = rec[q][v];
+      for (int q = 0; q < NQ; ++q)
 #pragma unroll
-    for (int v = 0; v < N; ++v) {
-      sref[v * T::NS + s] = ref[v]; sreflo[v * T::NS + s] = rlo[v]; sdfc[v * T::NS + s] = dfc[v];
+        for (int v = 0; v < N; ++v) smf[(q * N + v) * T::NS + s] = rec[q][v];
+#pragma unroll
+      for (int v = 0; v < N; ++v) {
+        sref[v * T::NS + s] = ref[v]; sreflo[v * T::NS + s] = rlo[v]; sdfcp[v * T::NS + s] = dfc[v];
+      }
     }
   }
   __syncthreads();
@@ -376,13 +400,29 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
     slot[t] = DIR == 0 ? (ry + t) * T::SA + tx : ry * T::SA + tx + t;
   // reference of this face and the other slots' reference offsets
   float ref[N], dref[5][N];
+  if constexpr (AOS) {
+    const float4* own = reinterpret_cast<const float4*>(smf + RS * slot[2]);
+    const float4 rh4 = own[NQ], rl4 = own[NQ + 1];
+    const float rh[N] = {rh4.x, rh4.y, rh4.z, rh4.w}, rl[N] = {rl4.x, rl4.y, rl4.z, rl4.w};
 #pragma unroll
-  for (int v = 0; v < N; ++v) {
-    ref[v] = sref[v * T::NS + slot[2]];
-    float rl = sreflo[v * T::NS + slot[2]];
+    for (int t = 0; t < 5; ++t) {
+      const float4* rw = reinterpret_cast<const float4*>(smf + RS * slot[t]);
+      const float4 h4 = rw[NQ], l4 = rw[NQ + 1];
+      const float h[N] = {h4.x, h4.y, h4.z, h4.w}, l[N] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-    for (int t = 0; t < 5; ++t)
-      dref[t][v] = (sref[v * T::NS + slot[t]] - ref[v]) + (sreflo[v * T::NS + slot[t]] - rl);
+      for (int v = 0; v < N; ++v) dref[t][v] = (h[v] - rh[v]) + (l[v] - rl[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < N; ++v) ref[v] = rh[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      ref[v] = sref[v * T::NS + slot[2]];
+      const float rl = sreflo[v * T::NS + slot[2]];
+#pragma unroll
+      for (int t = 0; t < 5; ++t)
+        dref[t][v] = (sref[v * T::NS + slot[t]] - ref[v]) + (sreflo[v * T::NS + slot[t]] - rl);
+    }
   }
   const float it = a.itanf;
   float F[N] = {0}, Ft[N] = {0}, dW0[N] = {0}, Wt[N] = {0}, Wtt[N] = {0};
@@ -392,37 +432,81 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   for (int g = 0; g < 3; ++g) {
     PointIn<float, 2> pin;
     float d0[N];
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      float s0 = 0, s1 = 0, s2 = 0, n0 = 0, n1 = 0, nn0 = 0;
-      float l0 = 0, l1 = 0, ln0 = 0, r0 = 0, r1 = 0, rn0 = 0;
+    if constexpr (AOS) {
+      // tangential quartic at Gauss point g: slot t's quantities of all four variables come
+      // in one 128-bit shared load each
+      float s0[N] = {0}, s1[N] = {0}, s2[N] = {0}, n0[N] = {0}, n1[N] = {0}, nn0[N] = {0};
 #pragma unroll
       for (int t = 0; t < 5; ++t) {
         const float w0 = TWf[g][0][t], w1 = TWf[g][1][t], w2 = TWf[g][2][t];
-        float q0 = smf[(0 * N + v) * T::NS + slot[t]] + dref[t][v];
-        float q1 = smf[(1 * N + v) * T::NS + slot[t]];
-        float q2 = smf[(2 * N + v) * T::NS + slot[t]];
-        s0 += w0 * q0; s1 += w1 * q0; s2 += w2 * q0;
-        n0 += w0 * q1; n1 += w1 * q1;
-        nn0 += w0 * q2;
-        if (WENO) {
-          float ql = smf[(3 * N + v) * T::NS + slot[t]] + dref[t][v];
-          float qld = smf[(4 * N + v) * T::NS + slot[t]];
-          float qr = smf[(5 * N + v) * T::NS + slot[t]] + dref[t][v];
-          float qrd = smf[(6 * N + v) * T::NS + slot[t]];
-          l0 += w0 * ql; l1 += w1 * ql; ln0 += w0 * qld;
-          r0 += w0 * qr; r1 += w1 * qr; rn0 += w0 * qrd;
+        const float4* rw = reinterpret_cast<const float4*>(smf + RS * slot[t]);
+        const float4 a0 = rw[0], a1 = rw[1], a2 = rw[2];
+        const float x0[N] = {a0.x, a0.y, a0.z, a0.w}, x1[N] = {a1.x, a1.y, a1.z, a1.w};
+        const float x2[N] = {a2.x, a2.y, a2.z, a2.w};
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          const float q0 = x0[v] + dref[t][v];
+          s0[v] += w0 * q0; s1[v] += w1 * q0; s2[v] += w2 * q0;
+          n0[v] += w0 * x1[v]; n1[v] += w1 * x1[v];
+          nn0[v] += w0 * x2[v];
         }
       }
-      d0[v] = s0;
-      pin.W0[v] = ref[v] + s0; pin.W0y[v] = s1 * it; pin.W0yy[v] = s2 * it * it;
-      pin.W0x[v] = n0; pin.W0xy[v] = n1 * it; pin.W0xx[v] = nn0;
-      if (WENO) {
-        pin.Wl[v] = ref[v] + l0; pin.Wly[v] = l1 * it; pin.Wlx[v] = ln0;
-        pin.Wr[v] = ref[v] + r0; pin.Wry[v] = r1 * it; pin.Wrx[v] = rn0;
-      } else {
-        pin.Wl[v] = pin.W0[v]; pin.Wly[v] = pin.W0y[v]; pin.Wlx[v] = n0;
-        pin.Wr[v] = pin.W0[v]; pin.Wry[v] = pin.W0y[v]; pin.Wrx[v] = n0;
+#pragma unroll
+      for (int v = 0; v < N; ++v) {
+        d0[v] = s0[v];
+        pin.W0[v] = ref[v] + s0[v]; pin.W0y[v] = s1[v] * it; pin.W0yy[v] = s2[v] * it * it;
+        pin.W0x[v] = n0[v]; pin.W0xy[v] = n1[v] * it; pin.W0xx[v] = nn0[v];
+        pin.Wl[v] = pin.W0[v]; pin.Wly[v] = pin.W0y[v]; pin.Wlx[v] = n0[v];
+        pin.Wr[v] = pin.W0[v]; pin.Wry[v] = pin.W0y[v]; pin.Wrx[v] = n0[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < N; ++v) {
+        float s0 = 0, s1 = 0, s2 = 0, n0 = 0, n1 = 0, nn0 = 0;
+        float l0 = 0, l1 = 0, ln0 = 0, r0 = 0, r1 = 0, rn0 = 0;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          const float w0 = TWf[g][0][t], w1 = TWf[g][1][t], w2 = TWf[g][2][t];
+          float q0 = smf[(0 * N + v) * T::NS + slot[t]] + dref[t][v];
+          float q1 = smf[(1 * N + v) * T::NS + slot[t]];
+          float q2 = smf[(2 * N + v) * T::NS + slot[t]];
+          s0 += w0 * q0; s1 += w1 * q0; s2 += w2 * q0;
+          n0 += w0 * q1; n1 += w1 * q1;
+          nn0 += w0 * q2;
+          if (WENO && !TANW) {
+            float ql = smf[(3 * N + v) * T::NS + slot[t]] + dref[t][v];
+            float qld = smf[(4 * N + v) * T::NS + slot[t]];
+            float qr = smf[(5 * N + v) * T::NS + slot[t]] + dref[t][v];
+            float qrd = smf[(6 * N + v) * T::NS + slot[t]];
+            l0 += w0 * ql; l1 += w1 * ql; ln0 += w0 * qld;
+            r0 += w0 * qr; r1 += w1 * qr; rn0 += w0 * qrd;
+          }
+        }
+        d0[v] = s0;
+        pin.W0[v] = ref[v] + s0; pin.W0y[v] = s1 * it; pin.W0yy[v] = s2 * it * it;
+        pin.W0x[v] = n0; pin.W0xy[v] = n1 * it; pin.W0xx[v] = nn0;
+        if (WENO && TANW) {
+          // tangential WENO-Z at the Gauss point for the non-equilibrium states
+          float ql[5], qld[5], qr[5], qrd[5];
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            ql[t] = smf[(3 * N + v) * T::NS + slot[t]] + dref[t][v];
+            qld[t] = smf[(4 * N + v) * T::NS + slot[t]];
+            qr[t] = smf[(5 * N + v) * T::NS + slot[t]] + dref[t][v];
+            qrd[t] = smf[(6 * N + v) * T::NS + slot[t]];
+          }
+          const float eps = a.epsf;
+          pin.Wl[v] = ref[v] + tan_weno<float, 0>(ql, g, eps); pin.Wly[v] = tan_weno<float, 1>(ql, g, eps) * it;
+          pin.Wlx[v] = tan_weno<float, 0>(qld, g, eps);
+          pin.Wr[v] = ref[v] + tan_weno<float, 0>(qr, g, eps); pin.Wry[v] = tan_weno<float, 1>(qr, g, eps) * it;
+          pin.Wrx[v] = tan_weno<float, 0>(qrd, g, eps);
+        } else if (WENO) {
+          pin.Wl[v] = ref[v] + l0; pin.Wly[v] = l1 * it; pin.Wlx[v] = ln0;
+          pin.Wr[v] = ref[v] + r0; pin.Wry[v] = r1 * it; pin.Wrx[v] = rn0;
+        } else {
+          pin.Wl[v] = pin.W0[v]; pin.Wly[v] = pin.W0y[v]; pin.Wlx[v] = n0;
+          pin.Wr[v] = pin.W0[v]; pin.Wry[v] = pin.W0y[v]; pin.Wrx[v] = n0;
+        }
       }
     }
     PointOut<float, 2> po;
@@ -436,8 +520,13 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   }
   if (!ok) atomicOr(a.status, ST_NONPHYSICAL);
   float dFc[N];   // reference-flux difference of the face's two cells (stage 1; phase A)
+  if constexpr (AOS) {
+    const float4 d4 = sdfc[slot[2]];
+    dFc[0] = d4.x; dFc[1] = d4.y; dFc[2] = d4.z; dFc[3] = d4.w;
+  } else {
 #pragma unroll
-  for (int v = 0; v < N; ++v) dFc[v] = sdfc[v * T::NS + slot[2]];
+    for (int v = 0; v < N; ++v) dFc[v] = sdfcp[v * T::NS + slot[2]];
+  }
   if (DIR == 1) {
     swap_uv_f<2>(F); swap_uv_f<2>(Ft); swap_uv_f<2>(dW0); swap_uv_f<2>(Wt); swap_uv_f<2>(Wtt); swap_uv_f<2>(dFc);
   }
@@ -457,11 +546,12 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
 // Linear Euler tiles: five blocks (20 warps) per SM, measured fastest for both stages (the
 // first stage spills a few bytes at that bound); the WENO-Z / viscous tiles are left to the
 // compiler.
-template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE, bool WALLS>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE, bool WALLS, bool TANW = false>
 __global__ void __launch_bounds__(TA32 * TB32, (WENO || VISC) ? 0 : 5)
 faces_2d_f32_kernel(FaceArgs32 a) {
   extern __shared__ float smf[];
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE, WALLS>(a, blockIdx.x, blockIdx.y, threadIdx.y * TA32 + threadIdx.x, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, false, FPT, STAGE, WALLS, TANW>(a, blockIdx.x, blockIdx.y,
+                                                                        threadIdx.y * TA32 + threadIdx.x, smf);
 }
 
 // ---------------------------------------------------------------------------

@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("eps_tau", ctypes.c_double), ("C_tau", ctypes.c_double),
                 ("use_graph", ctypes.c_int),
                 ("tau_mode", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p),
+                ("tan_mode", ctypes.c_int)]
 
 
 # Every symbol include/gks.h declares, with (restype, argtypes).
@@ -64,6 +65,7 @@ SIGNATURES = {
     "gks_steps_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _DP]),
     "gks_probe_alu_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
     "gks_probe_time_coefs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
+    "gks_probe_rcp64": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "gks_step_1d_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -154,7 +156,7 @@ class Solver:
                  y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
                  weno_eps: float = 1e-6, use_graph: bool = True, stream=None,
                  precision: int = PREC_FP64, tau_mode: int = 0, eps_tau: float = 0.01,
-                 C_tau: float = 1.0):
+                 C_tau: float = 1.0, tan_mode: int = 0):
         L = lib()
         o = default_opts()
         o.precision = precision
@@ -163,6 +165,7 @@ class Solver:
         o.weno_eps = weno_eps
         o.use_graph = 1 if use_graph else 0
         o.tau_mode = tau_mode
+        o.tan_mode = tan_mode
         o.eps_tau, o.C_tau = eps_tau, C_tau
         o.stream = stream
         self._h = L.gks_create(nx, ny, gamma, mu, Pr, order, recon, ctypes.byref(o))
@@ -274,6 +277,14 @@ def probe_time_coefs(theta, dt: float) -> np.ndarray:
     out = np.zeros((th.size, 4))
     _check(lib().gks_probe_time_coefs(th.ctypes.data_as(_DP), th.size, float(dt),
                                       out.ctypes.data_as(_DP)))
+    return out
+
+
+def probe_rcp64(x) -> np.ndarray:
+    """The FP32-bulk sweeps' FP64 reciprocal of each x, evaluated on the device."""
+    xx = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.zeros(xx.size)
+    _check(lib().gks_probe_rcp64(xx.ctypes.data_as(_DP), xx.size, out.ctypes.data_as(_DP)))
     return out
 
 

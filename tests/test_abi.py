@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 def test_default_opts():
     o = gks.default_opts()
     assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-6, 0.01, 1.0, 1)
-    assert o.tau_mode == 0 and o.stream is None
+    assert o.tau_mode == 0 and o.stream is None and o.tan_mode == 0
 
 
 def test_create_rejects_invalid_tau_mode():

@@ -12,10 +12,10 @@ from paper_1901_00261_gb300 import inputs
 
 @pytest.mark.parametrize("key", sorted(bench.KERNEL_MODEL))
 def test_roofline_block_for_every_modelled_launch(key):
-    form, name = key
+    path, form, name = key
     n, ms = 2048, 0.4
     issue_peak = 4 * 152 * 2070e6
-    r = bench.roofline(form, name, ms, n, n, 8, 1.25e12, 73e12, issue_peak)
+    r = bench.roofline(form, name, ms, n, n, 8, 1.25e12, 73e12, issue_peak, path=path)
     assert r["bound"] in ("alu", "hbm") and r["kernel"] == name
     assert r["unit"] in ("TFLOP/s", "GB/s")
     assert math.isclose(r["frac"], r["achieved"] / r["peak"], rel_tol=1e-12)
@@ -29,8 +29,10 @@ def test_roofline_block_for_every_modelled_launch(key):
         if o["bound"] != "issue":
             assert o["frac"] <= r["frac"]
     issue = [o for o in r["other_bounds"] if o["bound"] == "issue"]
-    assert len(issue) == 1
-    assert math.isclose(issue[0]["frac"], m["winstr"] / 32 * units / (ms * 1e-3) / issue_peak, rel_tol=1e-12)
+    assert len(issue) == ("winstr" in m)
+    if issue:
+        assert math.isclose(issue[0]["frac"], m["winstr"] / 32 * units / (ms * 1e-3) / issue_peak,
+                            rel_tol=1e-12)
     assert (r["traffic"] is None) == ("traffic" not in m)
 
 

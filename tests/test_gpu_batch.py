@@ -175,3 +175,58 @@ def test_batch_freezes_a_nonphysical_problem_and_keeps_the_rest():
     B.steps(dt2, 1)
     B.sync()
     assert_close_to_alone(B.get_state(2), run_alone(calm, dt2[2], 1), calm, "restarted problem")
+
+
+# FP32-bulk bounds of tests/test_gpu_fp32.py per problem class: (W, slopes), per step from
+# identical input against the FP64 reference (here the oracle), slopes relative to the scale
+# max|W|/dx of their difference quotient.
+ORACLE_BOUNDS = {"linear": (3e-8, 3e-7), "wenoz_1d": (2e-6, 2e-6), "wenoz_2d": (3e-7, 2e-6),
+                 "ns": (2e-5, 2e-5)}
+
+
+def _oracle_step(st, W, Wx, Wy, dt):
+    import oracle
+    O = oracle.Solver(st.nx, st.ny, st.gamma, st.mu, st.Pr, st.order, st.recon, st.bc_x, st.bc_y,
+                      st.x0, st.x1, st.y0, st.y1)
+    O.set_state(W, Wx, Wy)
+    O.step(dt)
+    return O.get_state()
+
+
+def test_batch_members_match_the_oracle_per_step():
+    """A mixed batch (1D WENO-Z Riemann problems from the batched workload's recipe, 2D
+    linear vortices, both orders, plus a 2D WENO-Z vortex and a Navier-Stokes shear layer):
+    for two consecutive steps each member's batch step from its current state is compared
+    with the FP64 oracle's step from the same state, within the FP32-bulk form's bounds."""
+    specs = inputs.batch_specs(8, seed=13, n1_range=(100, 400), n2_range=(16, 40))
+    states = [inputs.build_problem(s) for s in specs]
+    states += [inputs.isentropic_vortex_2d(24, order=8, recon=1, ny=20), inputs.shear_layer_2d(24)]
+    kinds = []
+    for st in states:
+        if st.mu > 0:
+            kinds.append("ns")
+        elif st.recon == 1:
+            kinds.append("wenoz_1d" if st.ny == 1 else "wenoz_2d")
+        else:
+            kinds.append("linear")
+    assert {"linear", "wenoz_1d"} <= set(kinds) and {6, 8} <= {st.order for st in states}
+    dts = dts_of(states)
+    B = gks.Batch(states)
+    for step in range(2):
+        before = [B.get_state(k) for k in range(len(states))]
+        B.steps(dts, 1)
+        for k, st in enumerate(states):
+            ref = _oracle_step(st, *before[k], dts[k])
+            got = B.get_state(k)
+            tw, ts = ORACLE_BOUNDS[kinds[k]]
+            Wr = ref[0]
+            for a_i, (a, b) in enumerate(zip(got, ref)):
+                if b is None:
+                    continue
+                for v in range(b.shape[0]):
+                    scale = np.abs(b[v]).max()
+                    if a_i > 0:
+                        scale = max(scale, np.abs(Wr[v]).max() / (st.dx if a_i == 1 else st.dy))
+                    err = np.abs(a[v] - b[v]).max() / max(scale, 1e-300)
+                    assert err <= (tw if a_i == 0 else ts), \
+                        f"step {step} problem {k} ({kinds[k]}, {st.nx}x{st.ny}) array {a_i} var {v}: {err:.3e}"

@@ -85,20 +85,33 @@ def test_fp32_bulk_conserves_exactly(make):
     assert np.abs(W.sum(axis=(1, 2)) - m0).max() <= 1e-13 * np.abs(st.W).sum(axis=(1, 2)).max()
 
 
+def _vortex_l1(n, prec, T=1.0):
+    st = inputs.isentropic_vortex_2d(n, order=8)
+    S = gks.Solver.from_state(st, precision=prec)
+    ns = math.ceil(T / (0.3 / S.max_wavespeed()))
+    S.steps(T / ns, ns)
+    W, _, _ = S.get_state()
+    return np.abs(W[0] - inputs.vortex_exact_avg(n, T)[0]).mean()
+
+
 @pytest.mark.parametrize("n", [128, 256])
 def test_fp32_bulk_vortex_accuracy_within_2x_of_fp64(n):
     """Isentropic vortex, 8th order, t = 1: L1 density error of the FP32-bulk form within a
-    factor 2 of the FP64 form (on finer grids FP32 rounding, ~2e-8 at t = 1, dominates)."""
-    res = {}
-    for prec in (gks.PREC_FP64, gks.PREC_FP32_BULK):
-        st = inputs.isentropic_vortex_2d(n, order=8)
-        S = gks.Solver.from_state(st, precision=prec)
-        T = 1.0
-        ns = math.ceil(T / (0.3 / S.max_wavespeed()))
-        S.steps(T / ns, ns)
-        W, _, _ = S.get_state()
-        res[prec] = np.abs(W[0] - inputs.vortex_exact_avg(n, T)[0]).mean()
-    assert res[gks.PREC_FP32_BULK] <= 2.0 * res[gks.PREC_FP64], res
+    factor 2 of the FP64 form.  The factor-2 claim holds up to 256^2 at t = 1; on finer grids
+    the FP32 rounding floor (next test) is above the FP64 form's truncation error."""
+    e64, e32 = _vortex_l1(n, gks.PREC_FP64), _vortex_l1(n, gks.PREC_FP32_BULK)
+    assert e32 <= 2.0 * e64, (e32, e64)
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_fp32_bulk_vortex_error_floor_on_fine_grids(n):
+    """The grids where the factor 2 is NOT met, pinned at their measured floor: at t = 1 the
+    FP32-bulk L1 density error stays at the single-precision rounding floor of ~2.8e-8
+    (measured on a GB300: 2.77e-8 at 512^2, where the FP64 form gives 5.34e-10, a ratio of
+    52), bounded here by 5e-8, while the FP64 form keeps converging below it."""
+    e64, e32 = _vortex_l1(n, gks.PREC_FP64), _vortex_l1(n, gks.PREC_FP32_BULK)
+    assert e32 <= 5e-8 and e64 < 1e-9, (e32, e64)
+    assert e32 > 2.0 * e64   # the documented limit of the factor-2 claim still stands
 
 
 def test_fp32_bulk_density_wave_error_floor():

@@ -73,3 +73,21 @@ def test_time_coefficients_match_their_definition(dt):
 def test_time_coefficient_probe_rejects_bad_theta():
     with pytest.raises(gks.GksError):
         gks.probe_time_coefs(np.array([1.0, 0.0]), 0.1)
+
+
+def test_rcp64_within_two_ulp_of_the_reciprocal():
+    """The FP64 reciprocal of the single-precision sweeps (a float seed and two Newton-Raphson
+    steps in FP64) against the correctly rounded 1/x, over the float-normal range where it is
+    used (densities and their products): at most 2 ulp of 1/x."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([np.logspace(-37, 37, 741), rng.uniform(0.05, 20.0, 4000),
+                        [1.0, 2.0, 0.1, 3.0, 7.0, 1.0 - 2.0 ** -52, 1.0 + 2.0 ** -52]])
+    got = gks.probe_rcp64(x)
+    want = 1.0 / x
+    ulp = np.spacing(want)
+    assert np.max(np.abs(got - want) / ulp) <= 2.0
+
+
+def test_rcp64_probe_rejects_null():
+    L = gks.lib()
+    assert L.gks_probe_rcp64(None, 1, None) == gks.GKS_EINVAL
