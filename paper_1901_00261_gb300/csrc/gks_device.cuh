@@ -336,7 +336,8 @@ struct TimeCoef { double a0, a1, b0, b1; };
 // Taylor coefficients of 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x) for
 // phi(y) = 1 - e^{-y}(1 + y) = sum_{k>=2} (-1)^k (k-1) y^k / k!, k = 2..21, and of
 // S(x) = 1 - e^{-x} = sum_{k>=1} (-1)^(k+1) x^k / k!, formed at compile time.  The series are
-// used for x < 1/2, where the first omitted term is below 1e-19 of the terms' magnitude
+// used for x < 1/2, where the first omitted term (of the truncation time_coefs picks for the
+// range of x) is below 1e-19 of the terms' magnitude
 // |4 phi(x)| + |phi(2x)| (resp. |phi(2x)| + |2 phi(x)|; for S, of S itself); from x = 1/2 on,
 // the closed form loses at most a few ulp of that magnitude to cancellation (1e-15 measured
 // against an 80-digit evaluation; at x -> 1 the series would leave 6e-14).
@@ -354,6 +355,24 @@ __host__ __device__ constexpr PhiSeries make_phi_series() {
   return c;
 }
 
+// 4 phi(x) - phi(2x), phi(2x) - 2 phi(x) and 1 - e^{-x} by their series up to x^K.
+template <int K>
+__device__ __forceinline__ void time_series(double x, double& pa, double& pb, double& S) {
+  constexpr PhiSeries C = make_phi_series();
+  double qa = C.a[K], qb = C.b[K], qs = C.s[K];
+#pragma unroll
+  for (int k = K - 1; k >= 2; --k) {
+    qa = fma(qa, x, C.a[k]);
+    qb = fma(qb, x, C.b[k]);
+    qs = fma(qs, x, C.s[k]);
+  }
+  qs = fma(qs, x, C.s[1]);
+  const double x2 = x * x;
+  pa = qa * x2;
+  pb = qb * x2;
+  S = qs * x;
+}
+
 // Arguments in terms of theta = tau/dt and x = (dt/2)/tau = 1/(2 theta) (both formed by the
 // caller in its arithmetic type; the cancellation is inside the formulas below, which run in
 // FP64): a0 = theta S (2 + S), b0 = -4 theta S^2 / dt, a1 = theta^2 dt pa, b1 = 4 theta^2 pb.
@@ -362,20 +381,12 @@ __device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt
   double S;        // 1 - e^{-x}
   double pa, pb;   // 4 phi(x) - phi(2x) and phi(2x) - 2 phi(x), phi(y) = 1 - e^{-y}(1+y)
   if (x < 0.5) {
-    // the three series, by Horner's rule in x in lockstep (x^2, resp. x, factored out)
-    constexpr PhiSeries C = make_phi_series();
-    double qa = C.a[21], qb = C.b[21], qs = C.s[21];
-#pragma unroll
-    for (int k = 20; k >= 2; --k) {
-      qa = fma(qa, x, C.a[k]);
-      qb = fma(qb, x, C.b[k]);
-      qs = fma(qs, x, C.s[k]);
-    }
-    qs = fma(qs, x, C.s[1]);
-    const double x2 = x * x;
-    pa = qa * x2;
-    pb = qb * x2;
-    S = qs * x;
+    // the three series, by Horner's rule in x in lockstep (x^2, resp. x, factored out),
+    // truncated after the last term that reaches 1e-19 of the magnitudes above: k = 15 for
+    // x < 1/8, 17 for x < 1/4, 21 for x < 1/2 (fewer dependent FP64 steps for small x)
+    if (x < 0.125) time_series<15>(x, pa, pb, S);
+    else if (x < 0.25) time_series<17>(x, pa, pb, S);
+    else time_series<21>(x, pa, pb, S);
   } else {
     // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
     S = x > 40.0 ? 1.0 : -expm1(-x);

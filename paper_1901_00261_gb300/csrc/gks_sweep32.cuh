@@ -205,15 +205,18 @@ __device__ __forceinline__ void sweep1d_f32_face(const FaceArgs32& a, int f) {
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     int c = map_index<WALLS>(f - 2 + o, a.nx, a.bcx);
+    // cell o = 1 is the reference cell: zero difference, only its slope is loaded
     float hi[N], lo[N], g[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); g[v] = ldf<CG>(a.Mn + v * ncell + c);
+      if (o != 1) { hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); }
+      else { hi[v] = 0.f; lo[v] = 0.f; }
+      g[v] = ldf<CG>(a.Mn + v * ncell + c);
     }
     if (walls) mirror_ghost<1, 0, float>(hi, lo, g, beyond_wall(f - 2 + o, a.nx, 2), false);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      in[v][o] = (hi[v] - ref[v]) + (lo[v] - rlo[v]);
+      in[v][o] = o == 1 ? 0.f : (hi[v] - ref[v]) + (lo[v] - rlo[v]);
       in[v][4 + o] = a.dnf * g[v];
     }
   }
@@ -328,16 +331,20 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
         long c;
         if (DIR == 0) c = (long)ct * a.nx + map_index<WALLS>(fn - 2 + o, a.nx, a.bcx);
         else c = (long)map_index<WALLS>(fn - 2 + o, a.ny, a.bcy) * a.nx + ct;
+        // cell o = 1 is the reference cell itself (same index map and mirror): its
+        // difference from the reference is zero and only its slope is loaded
         float hi[N], lo[N], g[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); g[v] = ldf<CG>(a.Mn + v * ncell + c);
+          if (o != 1) { hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); }
+          else { hi[v] = 0.f; lo[v] = 0.f; }
+          g[v] = ldf<CG>(a.Mn + v * ncell + c);
         }
         if (walls) mirror_ghost<2, DIR, float>(hi, lo, g, beyond_wall(fn - 2 + o, nnc, bcn), rt);
         if (DIR == 1) { swap_uv_f<2>(hi); swap_uv_f<2>(lo); swap_uv_f<2>(g); }
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          in[v][o] = (hi[v] - ref[v]) + (lo[v] - rlo[v]);
+          in[v][o] = o == 1 ? 0.f : (hi[v] - ref[v]) + (lo[v] - rlo[v]);
           in[v][4 + o] = a.dnf * g[v];
         }
       }
@@ -567,6 +574,20 @@ faces_2d_f32_kernel(FaceArgs32 a) {
 //     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
 //     place (each cell reads only its own state), and the mirror of W^{n+1}.
 // ---------------------------------------------------------------------------
+// float -> double on the integer pipes: the exponent rebiased (127 -> 1023) and the 23
+// significand bits moved to the top of the 52; exact for normal floats, inf and nan, and
+// zero; subnormal floats (|f| < 2^-126) become zero of the same sign.  The stage-2 update,
+// bound by the FP64 pipe, which also executes the FP32 -> FP64 conversions, uses it for the
+// single-precision parts of the new slopes.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+  unsigned hi = sgn | (ed << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) { hi = sgn; lo = 0u; }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
 template <int DIM>
 __device__ __forceinline__ void write_mirror(float* M, long c, long ncell, const double* w,
@@ -684,11 +705,11 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       double w = W0[v] - (Xr[v] - Xl[v]) * idx;
-      a.W[L + v * ncell + c] = fma(dWx[v], idx, (double)(dLx[v] * idxf));
+      a.W[L + v * ncell + c] = fma(dWx[v], idx, f2d_int(dLx[v] * idxf));
       M[2 * L + v * ncell + c] = (fWx[v] + dLx[v]) * idxf;   // (dW + dLT_{i+1/2} - dLT_{i-1/2}) / dx
       if (DIM == 2) {
         w -= (Yt[v] - Yb[v]) * idy;
-        a.W[2 * L + v * ncell + c] = fma(dWy[v], idy, (double)(dLy[v] * idyf));
+        a.W[2 * L + v * ncell + c] = fma(dWy[v], idy, f2d_int(dLy[v] * idyf));
         M[3 * L + v * ncell + c] = (fWy[v] + dLy[v]) * idyf;
       }
       a.W[v * ncell + c] = w;

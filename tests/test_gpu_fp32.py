@@ -103,13 +103,13 @@ def test_fp32_bulk_vortex_accuracy_within_2x_of_fp64(n):
     assert e32 <= 2.0 * e64, (e32, e64)
 
 
-@pytest.mark.parametrize("n", [512, 1024])
-def test_fp32_bulk_vortex_error_floor_on_fine_grids(n):
-    """The grids where the factor 2 is NOT met, pinned at their measured floor: at t = 1 the
-    FP32-bulk L1 density error stays at the single-precision rounding floor of ~2.8e-8
-    (measured on a GB300: 2.77e-8 at 512^2, where the FP64 form gives 5.34e-10, a ratio of
-    52), bounded here by 5e-8, while the FP64 form keeps converging below it."""
-    e64, e32 = _vortex_l1(n, gks.PREC_FP64), _vortex_l1(n, gks.PREC_FP32_BULK)
+def test_fp32_bulk_vortex_error_at_512_where_the_factor_2_fails():
+    """The first grid where the factor 2 is NOT met, pinned at its measured value: at t = 1
+    the FP32-bulk L1 density error is 2.77e-8 (GB300), the FP64 form's 5.34e-10, a ratio of
+    52; bounded here by 5e-8.  The cause is the weakly unstable high-frequency mode of the 2D
+    linear scheme (both forms, and the oracle), which grows from the rounding of each form:
+    ~1e-8 in FP32-bulk, ~1e-16 in FP64 (at 1024^2, t = 1: 1.1e-4 against 2.9e-9)."""
+    e64, e32 = _vortex_l1(512, gks.PREC_FP64), _vortex_l1(512, gks.PREC_FP32_BULK)
     assert e32 <= 5e-8 and e64 < 1e-9, (e32, e64)
     assert e32 > 2.0 * e64   # the documented limit of the factor-2 claim still stands
 

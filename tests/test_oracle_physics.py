@@ -24,6 +24,7 @@ scheme itself.
    cells.  A sign or flux mistake gives errors of order 0.1.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -196,3 +197,40 @@ def test_sound_attenuation(Pr, dim):
     c2 = _sound_attenuation_coefficient(0.005, Pr, dim)
     assert abs(c2 / expect - 1.0) < 1e-2, (c2, expect)
     assert abs(c2 - expect) < abs(c1 - expect), (c1, c2, expect)
+
+
+def _perturbed_uniform(n, ny, dim, U, V, seed=1):
+    rng = np.random.default_rng(seed)
+    nv = dim + 2
+    W = np.zeros((nv, ny, n))
+    W[0] = 1.0
+    W[1] = U
+    if dim == 2:
+        W[2] = V
+    W[-1] = 1.0 / 0.4 + 0.5 * (U * U + (V * V if dim == 2 else 0.0))
+    W += 1e-8 * rng.standard_normal(W.shape)
+    Wx = 1e-8 * n * rng.standard_normal(W.shape)
+    Wy = 1e-8 * ny * rng.standard_normal(W.shape) if dim == 2 else None
+    return W, Wx, Wy
+
+
+def test_2d_linear_scheme_has_a_weakly_growing_mode():
+    """A finding about the scheme as read (documented with its measurements): a 1e-8 random
+    perturbation of a uniform flow (U = V = 1) on a periodic 16 x 16 grid grows under the 2D
+    8th-order linear scheme at CFL 0.3 (more than 5x from step 100 to step 500; high diagonal
+    wavenumbers), while the same perturbation stays bounded under the 1D scheme."""
+    oracle.set_threads(os.cpu_count() or 1)
+    amps = {}
+    for dim, n, ny in ((1, 24, 1), (2, 16, 16)):
+        W, Wx, Wy = _perturbed_uniform(n, ny, dim, 1.0, 1.0)
+        S = oracle.Solver(n, ny, order=8, recon=0, x0=0, x1=1, y0=0, y1=ny / n)
+        S.set_state(W, Wx, Wy)
+        dt = 0.3 / S.max_wavespeed()
+        a = []
+        for k in range(500):
+            S.step(dt)
+            if k + 1 in (100, 500):   # after the first steps' adjustment of the random slopes
+                Wn = S.get_state()[0]
+                a.append(np.abs(Wn - Wn.mean(axis=(1, 2), keepdims=True)).max())
+        amps[dim] = a[1] / a[0]
+    assert amps[1] < 2.0 and amps[2] > 5.0, amps
