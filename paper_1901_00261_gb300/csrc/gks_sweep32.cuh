@@ -20,12 +20,26 @@
 
 namespace gks {
 
+// float -> double on the integer pipes: the exponent rebiased (127 -> 1023) and the 23
+// significand bits moved to the top of the 52; exact for normal floats, inf and nan, and
+// zero; subnormal floats (|f| < 2^-126) become zero of the same sign.  The FP64 pipe also
+// executes FP32 -> FP64 conversions and bounds the stage-2 update; the face epilogues and
+// the updates convert their single-precision parts with this instead.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+  unsigned hi = sgn | (ed << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) { hi = sgn; lo = 0u; }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // 1/x for a positive normal x within the float range: a single-precision seed refined by
 // two Newton-Raphson steps for f(r) = 1/r - x, r <- r + r (1 - x r), in FP64 (each squares
 // the relative error, from ~2^-23 to below FP64 rounding: within a few ulp of 1/x, tested
 // through gks_probe_rcp64).  The reference fluxes only; no IEEE rounding guarantee.
 __device__ __forceinline__ double rcp64(double x) {
-  double r = (double)__frcp_rn((float)x);
+  double r = f2d_int(__frcp_rn((float)x));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
@@ -165,7 +179,7 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
       // reference would leave ~1e-8 |rho U| instead, so the FP64 flux is set to zero there
       // (conservation of mass, energy and tangential momentum stays exact)
       const bool odd_at_wall = (ml || mr) && v != 1 + DIR;
-      o64[(long)v * nfaces + face] = odd_at_wall ? 0.0 : fma(dt, Fref[v], (double)dpsi[v]);
+      o64[(long)v * nfaces + face] = odd_at_wall ? 0.0 : fma(dt, Fref[v], f2d_int(dpsi[v]));
       o64[(long)(N + v) * nfaces + face] = wr[v] - wl[v];
     }
   } else {
@@ -173,7 +187,7 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       double* xi = o64 + (long)v * nfaces + face;
-      if (!((ml || mr) && v != 1 + DIR)) *xi = ldd<CG>(xi) + (double)(s3f * Ft[v]);
+      if (!((ml || mr) && v != 1 + DIR)) *xi = ldd<CG>(xi) + f2d_int(s3f * Ft[v]);
       float* lt = o32 + (1L * N + v) * nfaces + face;
       *lt = ldf<CG>(lt) + s3f * Wtt[v];
     }
@@ -574,20 +588,6 @@ faces_2d_f32_kernel(FaceArgs32 a) {
 //     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
 //     place (each cell reads only its own state), and the mirror of W^{n+1}.
 // ---------------------------------------------------------------------------
-// float -> double on the integer pipes: the exponent rebiased (127 -> 1023) and the 23
-// significand bits moved to the top of the 52; exact for normal floats, inf and nan, and
-// zero; subnormal floats (|f| < 2^-126) become zero of the same sign.  The stage-2 update,
-// bound by the FP64 pipe, which also executes the FP32 -> FP64 conversions, uses it for the
-// single-precision parts of the new slopes.
-__device__ __forceinline__ double f2d_int(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
-  unsigned hi = sgn | (ed << 20) | (m >> 3), lo = m << 29;
-  if (e == 0u) { hi = sgn; lo = 0u; }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
 template <int DIM>
 __device__ __forceinline__ void write_mirror(float* M, long c, long ncell, const double* w,
