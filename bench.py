@@ -61,18 +61,18 @@ KERNEL_MODEL = {
     ("linear_euler", "fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
     ("linear_euler", "fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
     ("linear_euler", "fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
-    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2153.1, "f64": 35.0, "traffic": 160.0,
-                                                 "winstr": 2459},
-    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2071.5, "f64": 35.0, "traffic": 163.0,
-                                                 "winstr": 2220},
+    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 157.5,
+                                                 "winstr": 2303},
+    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 160.2,
+                                                 "winstr": 2087},
     ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
-                                                "traffic": 249.0, "winstr": 408},
-    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1847.6, "f64": 4.0, "traffic": 108.0,
-                                                 "winstr": 1924},
-    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1765.0, "f64": 4.0, "traffic": 109.0,
-                                                 "winstr": 1717},
+                                                "traffic": 247.6, "winstr": 408},
+    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1826.6, "f64": 4.0, "traffic": 110.8,
+                                                 "winstr": 1848},
+    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1750.0, "f64": 4.0, "traffic": 114.0,
+                                                 "winstr": 1651},
     ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
-                                                "traffic": 343.0, "winstr": 656},
+                                                "traffic": 342.9, "winstr": 703},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face from a 1024^2 capture
     ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 11501.0, "f64": 427.0},
