@@ -228,7 +228,9 @@ int gks_batch_sync(gks_batch* b);
 /* out[i] (n ints) = GKS_OK or GKS_ENONPHYSICAL for problem i.  Synchronises; returns
  * GKS_ETIMEOUT if a dependency wait ran out. */
 int gks_batch_problem_status(gks_batch* b, int* out);
-/* Tile shape of the persistent launch: faces (cells) per thread 1 or 2, resident blocks per SM. */
+/* Tile shape of the persistent launch: faces (cells) per thread 1, 2 or 4 (2D sweep tiles of
+ * 32 x 4, 32 x 8 or 32 x 16 faces; 1D and update items of 128, 256 or 512), and resident
+ * blocks per SM (1 .. the occupancy limit of that shape). */
 int gks_batch_config(gks_batch* b, int* faces_per_thread, int* blocks_per_sm);
 int gks_batch_set_config(gks_batch* b, int faces_per_thread, int blocks_per_sm);
 /* Autotuner: time `steps` steps for every tile shape candidate on this batch (the states are

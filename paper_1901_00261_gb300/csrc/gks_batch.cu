@@ -21,9 +21,11 @@
 // state (rho <= 0 or p <= 0) is frozen from then on (its items only signal completion), so
 // one failing problem neither stops nor perturbs the others; it is reported by index.
 //
-// The autotuner times the persistent launch for each (faces per thread of the 2D sweep
-// tiles, resident blocks per SM) candidate on the batch itself and keeps the fastest; the
-// choice is cached per batch shape.
+// The autotuner times the persistent launch for each (tile shape, resident blocks per SM)
+// candidate on the batch itself and keeps the fastest; the choice is cached per batch shape.
+// Tile shapes: 1, 2 or 4 face rows per thread, i.e. 2D sweep tiles of 32 x 4, 32 x 8 or
+// 32 x 16 faces (tangential halo overhead 2, 1.5 or 1.25 reconstructions per face against the
+// number of items to balance) and 1D / update items of 128, 256 or 512 faces or cells.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -35,161 +37,21 @@
 #include <vector>
 
 #include "../../include/gks.h"
-#include "gks_sweep32.cuh"
+#include "gks_batch.cuh"
 
 namespace gks {
 
-enum : unsigned int { ST_TIMEOUT = 4u };
-
-struct BatchProblem {
-  FaceArgs32 ax[2], ay[2];   // x / y sweeps, stage 1 and 2
-  UpdateArgs32 up;
-  int dim, order, recon;
-  int tiles_x, tiles_y, tiles_u;   // items per sweep direction / update (per stage)
-  int tbx_x, tbx_y;                // tiles along x of the 2D x / y sweep grids
-  unsigned need[4];                // items per phase
-};
-
-struct BatchArgs {
-  const BatchProblem* probs;
-  const int4* items;     // (problem, phase, kind, tile); kind 0 x sweep, 1 y sweep, 2 update
-  int nitems;
-  unsigned* counter;
-  unsigned* done;        // [nprob][4]
-  unsigned* status;      // [0]: batch-wide flags (ST_TIMEOUT); [1 + p]: flags of problem p
-  long long spin_cycles;
-};
-
-// Item dispatch.  CLASS 0: 1D (linear / WENO-Z, Euler) and 2D linear Euler problems;
-// CLASS 1: every problem kind (2D WENO-Z, Navier-Stokes).
-template <int CLASS, int FPT>
-__device__ __forceinline__ void run_item(const BatchProblem& P, int phase, int kind, int tile, int tid,
-                                         float* smf) {
-  const int stage = phase < 2 ? 0 : 1;
-  if (phase == 0 || phase == 2) {
-    const FaceArgs32& a = kind == 0 ? P.ax[stage] : P.ay[stage];
-    const bool visc = a.P.mu > 0.0;
-    if (P.dim == 1) {
-      const int base = tile * (TA32 * TB32 * FPT);
-#pragma unroll 1
-      for (int r = 0; r < FPT; ++r) {
-        const int f = base + r * (TA32 * TB32) + tid;
-        // the MSMD stage (index 0 / 1) picks the stage-1 / stage-2 instantiation
-#define GKS_SWEEP1D(O, WN, VS) \
-  (stage == 0 ? sweep1d_f32_face_call<O, WN, VS, 1>(a, f) : sweep1d_f32_face_call<O, WN, VS, 2>(a, f))
-        if (P.order == 6) {
-          if (P.recon == 0) GKS_SWEEP1D(6, false, false);
-          else if (CLASS == 1 && visc) GKS_SWEEP1D(6, true, true);
-          else GKS_SWEEP1D(6, true, false);
-        } else {
-          if (P.recon == 0) GKS_SWEEP1D(8, false, false);
-          else if (CLASS == 1 && visc) GKS_SWEEP1D(8, true, true);
-          else GKS_SWEEP1D(8, true, false);
-        }
-      }
-#undef GKS_SWEEP1D
-      return;
-    }
-    const int tbx = kind == 0 ? P.tbx_x : P.tbx_y;
-    const int bx = tile % tbx, by = tile / tbx;
-#define GKS_SWEEP2D(O, WN, VS, D)                                          \
-  (stage == 0 ? sweep2d_f32_tile_call<O, WN, VS, D, FPT, 1>(a, bx, by, tid, smf) \
-              : sweep2d_f32_tile_call<O, WN, VS, D, FPT, 2>(a, bx, by, tid, smf))
-    if (CLASS == 0) {
-      if (kind == 0) { if (P.order == 6) GKS_SWEEP2D(6, false, false, 0); else GKS_SWEEP2D(8, false, false, 0); }
-      else { if (P.order == 6) GKS_SWEEP2D(6, false, false, 1); else GKS_SWEEP2D(8, false, false, 1); }
-    } else {
-      const bool weno = P.recon == 1;
-      if (kind == 0) {
-        if (P.order == 6) {
-          if (weno) { if (visc) GKS_SWEEP2D(6, true, true, 0); else GKS_SWEEP2D(6, true, false, 0); }
-          else { if (visc) GKS_SWEEP2D(6, false, true, 0); else GKS_SWEEP2D(6, false, false, 0); }
-        } else {
-          if (weno) { if (visc) GKS_SWEEP2D(8, true, true, 0); else GKS_SWEEP2D(8, true, false, 0); }
-          else { if (visc) GKS_SWEEP2D(8, false, true, 0); else GKS_SWEEP2D(8, false, false, 0); }
-        }
-      } else {
-        if (P.order == 6) {
-          if (weno) { if (visc) GKS_SWEEP2D(6, true, true, 1); else GKS_SWEEP2D(6, true, false, 1); }
-          else { if (visc) GKS_SWEEP2D(6, false, true, 1); else GKS_SWEEP2D(6, false, false, 1); }
-        } else {
-          if (weno) { if (visc) GKS_SWEEP2D(8, true, true, 1); else GKS_SWEEP2D(8, true, false, 1); }
-          else { if (visc) GKS_SWEEP2D(8, false, true, 1); else GKS_SWEEP2D(8, false, false, 1); }
-        }
-      }
-    }
-#undef GKS_SWEEP2D
-    return;
-  }
-  // cell updates: FPT x 128 cells per item
-  const long base = (long)tile * (TA32 * TB32 * FPT);
-#pragma unroll 1
-  for (int r = 0; r < FPT; ++r) {
-    const long c = base + r * (TA32 * TB32) + tid;
-    if (P.dim == 1) {
-      if (phase == 1) update_f32_cell_call<1, 1>(P.up, c); else update_f32_cell_call<1, 2>(P.up, c);
-    } else {
-      if (phase == 1) update_f32_cell_call<2, 1>(P.up, c); else update_f32_cell_call<2, 2>(P.up, c);
-    }
-  }
-}
-
-// Class 0 (1D and 2D linear Euler): five blocks per SM (102 registers) measured fastest.
-template <int CLASS, int FPT>
-__global__ void __launch_bounds__(TA32 * TB32, CLASS == 0 ? 5 : 0) batch_kernel(BatchArgs b) {
-  extern __shared__ float smf[];
-  __shared__ int s_item, s_abort, s_skip;
-  const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) {
-      const int it = (int)atomicAdd(b.counter, 1u);
-      int abort = 0, skip = 0;
-      if (it < b.nitems) {
-        const int4 w = b.items[it];
-        if (w.y > 0) {
-          // wait for every item of the previous phase of this problem (bounded)
-          const volatile unsigned* flag = b.done + 4 * w.x + (w.y - 1);
-          const unsigned need = b.probs[w.x].need[w.y - 1];
-          const long long t0 = clock64();
-          while (*flag < need) {
-            if (clock64() - t0 > b.spin_cycles) { atomicOr(b.status, ST_TIMEOUT); abort = 1; break; }
-            __nanosleep(100);
-          }
-          __threadfence();
-        }
-        // a problem that has met a non-physical state is frozen: its items only signal
-        skip = ((volatile unsigned*)b.status)[1 + w.x] != 0u;
-      }
-      s_item = it;
-      s_abort = abort;
-      s_skip = skip;
-    }
-    __syncthreads();
-    const int it = s_item;
-    if (it >= b.nitems || s_abort) break;
-    const int4 w = b.items[it];
-    if (!s_skip) run_item<CLASS, FPT>(b.probs[w.x], w.y, w.z, w.w, tid, smf);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) atomicAdd(b.done + 4 * w.x + w.y, 1u);
-  }
-}
-
-template <int CLASS, int FPT>
-size_t batch_smem() {
-  const size_t s0 = Tile32<0, FPT>::smem_bytes(CLASS != 0), s1 = Tile32<1, FPT>::smem_bytes(CLASS != 0);
-  return s0 > s1 ? s0 : s1;
-}
-
-typedef void (*BatchKernelFn)(BatchArgs);
+// Faces (cells) per thread of the tile shapes the autotuner searches: 2D sweep tiles of
+// 32 x 4, 32 x 8 and 32 x 16 faces.
+constexpr int FPT_CHOICES[3] = {1, 2, 4};
+constexpr int NFPT = 3;
+inline int fpt_index(int fpt) { return fpt == 1 ? 0 : (fpt == 2 ? 1 : (fpt == 4 ? 2 : -1)); }
 
 BatchKernelFn batch_kernel_fn(int cls, int fpt) {
-  if (cls == 0) return fpt == 1 ? batch_kernel<0, 1> : batch_kernel<0, 2>;
-  return fpt == 1 ? batch_kernel<1, 1> : batch_kernel<1, 2>;
+  return fpt == 1 ? batch_kernel_fpt1(cls) : (fpt == 2 ? batch_kernel_fpt2(cls) : batch_kernel_fpt4(cls));
 }
 size_t batch_smem_of(int cls, int fpt) {
-  if (cls == 0) return fpt == 1 ? batch_smem<0, 1>() : batch_smem<0, 2>();
-  return fpt == 1 ? batch_smem<1, 1>() : batch_smem<1, 2>();
+  return fpt == 1 ? batch_smem_fpt1(cls) : (fpt == 2 ? batch_smem_fpt2(cls) : batch_smem_fpt4(cls));
 }
 
 }  // namespace gks
@@ -229,8 +91,8 @@ struct gks_batch {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   gks::BatchProblem* dprob = nullptr;
-  int4* ditems[2] = {nullptr, nullptr};   // work-lists for fpt 1 and 2
-  int nitems[2] = {0, 0};
+  int4* ditems[gks::NFPT] = {nullptr, nullptr, nullptr};   // work-lists for fpt 1, 2, 4
+  int nitems[gks::NFPT] = {0, 0, 0};
   unsigned* dcount = nullptr;   // [0] counter, [1..4n] done
   unsigned* dstatus = nullptr;
   double* ddt = nullptr;
@@ -239,7 +101,7 @@ struct gks_batch {
   std::vector<gks::StepTimes> times;   // host copy of the per-problem step constants
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int fpt = 1, blocks_per_sm = 0, max_blocks_per_sm[2] = {0, 0}, sms = 0;
+  int fpt = 1, blocks_per_sm = 0, max_blocks_per_sm[gks::NFPT] = {0, 0, 0}, sms = 0;
   bool cooperative = true;
   long long spin_cycles = 4000000000LL;   // wait budget of a dependency (~2 s at 2 GHz)
   cudaGraph_t graph = nullptr;
@@ -295,7 +157,7 @@ int upload_problems(gks_batch* B, int fpt) {
 }
 
 int enqueue_batch_step(gks_batch* B) {
-  const int fi = B->fpt == 1 ? 0 : 1;
+  const int fi = gks::fpt_index(B->fpt);
   cudaError_t e = cudaMemsetAsync(B->dcount, 0, sizeof(unsigned) * (1 + 4 * B->n), B->stream);
   if (e != cudaSuccess) return bcuda(e, "batch counters");
   gks::BatchArgs a;
@@ -325,8 +187,8 @@ void drop_graph(gks_batch* B) {
 }
 
 int set_config(gks_batch* B, int fpt, int bps) {
-  if (fpt != 1 && fpt != 2) return bfail(GKS_EINVAL, "faces per thread must be 1 or 2");
-  const int fi = fpt == 1 ? 0 : 1;
+  const int fi = gks::fpt_index(fpt);
+  if (fi < 0) return bfail(GKS_EINVAL, "faces per thread must be 1, 2 or 4");
   if (bps < 1 || bps > B->max_blocks_per_sm[fi]) return bfail(GKS_EINVAL, "blocks per SM out of range");
   if (fpt != B->fpt) {
     int rc = upload_problems(B, fpt);
@@ -460,9 +322,9 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     P.tbx_y = (q.nx + gks::TA32 - 1) / gks::TA32;
   }
   // work-lists for both tile shapes
-  for (int fi = 0; fi < 2; ++fi) {
+  for (int fi = 0; fi < gks::NFPT; ++fi) {
     std::vector<int4> items;
-    build_items(B, fi + 1, items);
+    build_items(B, gks::FPT_CHOICES[fi], items);
     B->nitems[fi] = (int)items.size();
     e = cudaMalloc((void**)&B->ditems[fi], sizeof(int4) * std::max<size_t>(items.size(), 1));
     if (e == cudaSuccess) e = cudaMemcpyAsync(B->ditems[fi], items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, B->stream);
@@ -475,10 +337,11 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   B->cooperative = coop != 0;
-  for (int fi = 0; fi < 2; ++fi) {
-    size_t sm = gks::batch_smem_of(B->cls, fi + 1);
-    e = cudaFuncSetAttribute(gks::batch_kernel_fn(B->cls, fi + 1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->max_blocks_per_sm[fi], gks::batch_kernel_fn(B->cls, fi + 1), gks::TA32 * gks::TB32, sm);
+  for (int fi = 0; fi < gks::NFPT; ++fi) {
+    const int f = gks::FPT_CHOICES[fi];
+    size_t sm = gks::batch_smem_of(B->cls, f);
+    e = cudaFuncSetAttribute(gks::batch_kernel_fn(B->cls, f), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->max_blocks_per_sm[fi], gks::batch_kernel_fn(B->cls, f), gks::TA32 * gks::TB32, sm);
     if (e != cudaSuccess || B->max_blocks_per_sm[fi] < 1) { bcuda(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "batch occupancy"); gks_batch_destroy(B); return nullptr; }
   }
   B->fpt = 0;
@@ -627,8 +490,9 @@ int gks_batch_autotune(gks_batch* B, const double* dt, int steps, char* report, 
   int bf = B->fpt, bb = B->blocks_per_sm;
   std::string rep = "fpt bps ms_per_step\n";
   int rc = GKS_OK;
-  for (int fpt = 1; fpt <= 2 && rc == GKS_OK; ++fpt) {
-    const int maxb = B->max_blocks_per_sm[fpt - 1];
+  for (int fi = 0; fi < gks::NFPT && rc == GKS_OK; ++fi) {
+    const int fpt = gks::FPT_CHOICES[fi];
+    const int maxb = B->max_blocks_per_sm[fi];
     for (int bps = 1; bps <= maxb && rc == GKS_OK; ++bps) {
       rc = set_config(B, fpt, bps);
       if (rc != GKS_OK) break;
@@ -722,7 +586,7 @@ void gks_batch_destroy(gks_batch* B) {
   drop_graph(B);
   if (B->arena) cudaFree(B->arena);
   if (B->dprob) cudaFree(B->dprob);
-  for (int fi = 0; fi < 2; ++fi) if (B->ditems[fi]) cudaFree(B->ditems[fi]);
+  for (int fi = 0; fi < gks::NFPT; ++fi) if (B->ditems[fi]) cudaFree(B->ditems[fi]);
   if (B->dcount) cudaFree(B->dcount);
   if (B->dstatus) cudaFree(B->dstatus);
   if (B->ddt) cudaFree(B->ddt);

@@ -63,13 +63,25 @@ def dts_of(states):
     return np.array(out)
 
 
-@pytest.mark.parametrize("fpt", [1, 2])
+def set_config_fitting(B, fpt, bps):
+    """Tile shape `fpt` with the most resident blocks per SM up to `bps` that fit (taller tiles
+    take more shared memory)."""
+    for b in range(bps, 0, -1):
+        try:
+            B.set_config(fpt, b)
+            return b
+        except gks.GksError:
+            continue
+    raise AssertionError(f"no block count fits tile shape {fpt}")
+
+
+@pytest.mark.parametrize("fpt", [1, 2, 4])
 def test_batch_matches_individual_runs(fpt):
     states = mixed_states()
     dts = dts_of(states)
     B = gks.Batch(states)
     _, maxb = B.config()
-    B.set_config(fpt, maxb)
+    set_config_fitting(B, fpt, maxb)
     B.steps(dts, 3)
     for k, st in enumerate(states):
         assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 3), st,
@@ -80,9 +92,9 @@ def test_batch_tile_shapes_and_occupancy_agree():
     states = mixed_states(6, seed=9)
     dts = dts_of(states)
     results = []
-    for fpt, bps in ((1, 1), (2, 2), (1, 3)):
+    for fpt, bps in ((1, 1), (2, 2), (1, 3), (4, 1), (4, 2)):
         B = gks.Batch(states)
-        B.set_config(fpt, min(bps, B.config()[1]))
+        set_config_fitting(B, fpt, min(bps, B.config()[1]))
         B.steps(dts, 2)
         results.append([B.get_state(k) for k in range(len(states))])
     for other in results[1:]:
@@ -111,7 +123,8 @@ def test_autotune_restores_state_and_keeps_results():
     report = B.autotune(dts, steps=2)
     assert "chosen" in report
     fpt, bps = B.config()
-    assert fpt in (1, 2) and bps >= 1
+    assert fpt in (1, 2, 4) and bps >= 1
+    assert any(line.startswith("4 ") for line in report.splitlines())   # 32 x 16 tiles were timed
     B.steps(dts, 2)
     for k, st in enumerate(states):
         assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 2), st, f"problem {k}")
