@@ -81,6 +81,8 @@ def lib():
             L.orc_set_eq_mode.argtypes = [c_void, c_int]
             L.orc_set_char_mode.argtypes = [c_void, c_int]
             L.orc_set_tan_mode.argtypes = [c_void, c_int]
+            L.orc_set_walls.argtypes = [c_void, dp, dp]
+            L.orc_iso_ghost.argtypes = [c_void, c_int, c_int, c_int, dp, dp]
             L.orc_tan_weno.argtypes = [dp, c_int, c_int, c_double, dp]
             L.orc_tan_weno.restype = c_double
             L.orc_set_state.argtypes = [c_void, dp, dp, dp]
@@ -232,7 +234,8 @@ class Solver:
                  order: int = 6, recon: int = 0, bc_x: int = 0, bc_y: int = 0,
                  x0: float = 0.0, x1: float = 1.0, y0: float = 0.0, y1: float = 1.0,
                  weno_eps: float = 1e-6, tau_mode: int = 0, flux_mode: int = 0,
-                 eq_mode: int = 1, char_mode: int = 0, tan_mode: int = 0):
+                 eq_mode: int = 1, char_mode: int = 0, tan_mode: int = 0,
+                 wall_T=(1.0, 1.0, 1.0, 1.0), wall_u=(0.0, 0.0, 0.0, 0.0)):
         self.nx, self.ny = nx, ny
         self.dim = 2 if ny > 1 else 1
         self.nv = self.dim + 2
@@ -243,6 +246,9 @@ class Solver:
         lib().orc_set_eq_mode(self._h, int(eq_mode))
         lib().orc_set_char_mode(self._h, int(char_mode))
         lib().orc_set_tan_mode(self._h, int(tan_mode))
+        wt = np.ascontiguousarray(wall_T, dtype=np.float64)
+        wu = np.ascontiguousarray(wall_u, dtype=np.float64)
+        lib().orc_set_walls(self._h, _p(wt), _p(wu))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -280,3 +286,13 @@ class Solver:
 
     def max_wavespeed(self) -> float:
         return float(lib().orc_max_wavespeed(self._h))
+
+    def iso_ghost(self, axis: int, side: int, normal: bool, w, d):
+        """Ghost of an isothermal wall (bc 3) for the mirror cell's conservative values w and
+        their derivatives d along the stencil (across the wall when normal).  axis 1 = x,
+        2 = y; side 0 = the low wall, 1 = the high one.  Returns (w_ghost, d_ghost)."""
+        w = np.array(w, dtype=np.float64)
+        d = np.array(d, dtype=np.float64)
+        if lib().orc_iso_ghost(self._h, int(axis), int(side), int(bool(normal)), _p(w), _p(d)) != 0:
+            raise ValueError("bad wall")
+        return w, d

@@ -67,6 +67,17 @@
 //       normal to the wall of every other variable (even functions across the mirror have
 //       odd derivatives), while the normal momentum's normal derivative keeps its sign.
 //       Derivatives along the wall keep the sign of their variable.
+//   R25 isothermal no-slip wall (bc 3; the lid-driven cavity of Sec. 5, "isothermal and
+//       nonslip"): ghost cell k outside the wall carries the primitive state of the mirror
+//       cell k inside with the same pressure (no pressure gradient normal to the wall), the
+//       velocity reflected through the wall's velocity (normal component negated,
+//       tangential u_t -> 2 u_w - u_t) and the temperature p/rho reflected through the
+//       wall's (T -> 2 T_w - T), so that the wall sees the no-slip velocity and T_w at second
+//       order; the density is p / T of the ghost.  The ghost's derivatives follow from the
+//       mirror: along the wall normal the pressure's changes sign and the velocity's and
+//       temperature's keep theirs; along the wall the opposite.  Cell
+//       averages are treated as point values in this map (the boundary is low order).  A cell
+//       beyond two walls (a corner) takes the x wall's map first, then the y wall's.
 //   R23 the equilibrium state g0 takes its value from the collision of the two initial
 //       states, W0 = int_{u>0} psi g_l + int_{u<0} psi g_r (identical to the linear
 //       reconstruction when the scheme is linear), and its derivatives from the compact
@@ -741,6 +752,9 @@ void euler_right_eigvecs(int dim, double gamma, const double* W, double* R) {
 struct Solver {
   int nx, ny, dim, nv, order, recon, bcx, bcy;
   int char_mode = 0;   // R8: 0 = characteristic variables at the mean state, 1 = component-wise
+  // isothermal walls (bc 3, R25): temperature p/rho and tangential velocity of the walls at
+  // x0, x1, y0, y1
+  double wall_T[4] = {1.0, 1.0, 1.0, 1.0}, wall_u[4] = {0.0, 0.0, 0.0, 0.0};
   int tan_mode = 0;    // R9: 0 = tangential quartic for every quantity, 1 = WENO-Z for the
                        // non-equilibrium states (tan_weno)
   double x0, x1, y0, y1, dx, dy, weno_eps;
@@ -753,7 +767,7 @@ inline long cidx(const Solver& S, int v, int j, int i) { return ((long)v * S.ny 
 
 int map_index(int i, int n, int bc) {
   if (bc == 0) { i %= n; if (i < 0) i += n; return i; }
-  if (bc == 2) {
+  if (bc == 2 || bc == 3) {
     // mirror about the wall: cell -1 is cell 0, cell n is cell n - 1, ...
     if (i < 0) i = -1 - i;
     if (i >= n) i = 2 * n - 1 - i;
@@ -764,6 +778,44 @@ int map_index(int i, int n, int bc) {
 
 // True when index i lies beyond a reflecting wall (its cell is a mirror image, R24).
 bool is_mirror(int i, int n, int bc) { return bc == 2 && (i < 0 || i >= n); }
+
+// True when index i lies beyond an isothermal no-slip wall (bc 3, R25).
+bool is_iso(int i, int n, int bc) { return bc == 3 && (i < 0 || i >= n); }
+
+// Ghost of an isothermal no-slip wall (R25) normal to axis `axis` (1 = x, 2 = y), at the
+// domain's low (side 0) or high (side 1) end: w the conservative state of the mirror cell
+// (global frame), d its derivatives along the stencil direction, which is normal to the wall
+// when `normal`, along it otherwise.  Both are replaced by the ghost's.
+void iso_ghost(const Solver& S, int axis, int side, bool normal, double* w, double* d) {
+  const int dim = S.dim, n = S.nv;
+  const double g1 = S.ph.gamma - 1.0;
+  const int wi = 2 * (axis - 1) + side;
+  const double Tw = S.wall_T[wi], uw = S.wall_u[wi];
+  // primitives and their derivatives along the stencil direction
+  double rho = w[0], u[2] = {w[1] / rho, dim == 2 ? w[2] / rho : 0.0};
+  double ke = 0.5 * (u[0] * u[0] + u[1] * u[1]);
+  double p = g1 * (w[n - 1] - rho * ke), T = p / rho;
+  double drho = d[0], du[2] = {(d[1] - u[0] * drho) / rho, dim == 2 ? (d[2] - u[1] * drho) / rho : 0.0};
+  double dke = u[0] * du[0] + u[1] * du[1];
+  double dp = g1 * (d[n - 1] - drho * ke - rho * dke), dT = (dp - T * drho) / rho;
+  // the map: normal velocity component `axis - 1` negated, the tangential one reflected
+  // through u_w, T through T_w; derivative signs per R25
+  const int an = axis - 1, at = 1 - an;
+  const double sn = normal ? -1.0 : 1.0;   // sign that the mirror gives an even quantity
+  double ug[2], dug[2];
+  ug[an] = -u[an]; dug[an] = -sn * du[an];
+  ug[at] = 2.0 * uw - u[at]; dug[at] = -sn * du[at];
+  if (dim == 1) { ug[1] = 0.0; dug[1] = 0.0; }
+  double Tg = 2.0 * Tw - T, dTg = -sn * dT;
+  double pg = p, dpg = sn * dp;
+  double rg = pg / Tg, drg = (dpg - rg * dTg) / Tg;
+  // back to conservative variables
+  double keg = 0.5 * (ug[0] * ug[0] + ug[1] * ug[1]), dkeg = ug[0] * dug[0] + ug[1] * dug[1];
+  w[0] = rg; d[0] = drg;
+  for (int c = 0; c < dim; ++c) { w[1 + c] = rg * ug[c]; d[1 + c] = drg * ug[c] + rg * dug[c]; }
+  w[n - 1] = pg / g1 + rg * keg;
+  d[n - 1] = dpg / g1 + drg * keg + rg * dkeg;
+}
 
 // Mirror image of a ghost cell across a wall normal to axis `axis` (1 = x, 2 = y; the
 // momentum component with that index changes sign), for a stencil running across the
@@ -902,17 +954,25 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
   const int nx = S.nx, ny = S.ny, n = S.nv, dim = S.dim;
   bool ok = true;
 
-  // ---- x faces: face f at x_{f-1/2}, f = 0..nx, rows j = 0..ny-1 ----
-  std::vector<FaceRecon> rx((size_t)(nx + 1) * ny);
+  // ---- x faces: face f at x_{f-1/2}, f = 0..nx, rows j = 0..ny-1; with isothermal walls
+  // in y (R25) also the four ghost rows j = -2, -1, ny, ny + 1, built from ghost cells ----
+  const bool isoy = dim == 2 && S.bcy == 3;
+  const int nrx = isoy ? ny + 4 : ny;
+  std::vector<FaceRecon> rx((size_t)(nx + 1) * nrx);
 #pragma omp parallel for schedule(static)
-  for (long idx = 0; idx < (long)(nx + 1) * ny; ++idx) {
-    int f = (int)(idx % (nx + 1)), j = (int)(idx / (nx + 1));
+  for (long idx = 0; idx < (long)(nx + 1) * nrx; ++idx) {
+    int f = (int)(idx % (nx + 1)), k = (int)(idx / (nx + 1));
+    int j = k < ny ? k : (k - ny < 2 ? k - ny - 2 : ny + (k - ny - 2));   // ghost rows after the interior
+    int jm = map_index(j, ny, S.bcy);
     double in8[4][8];
     for (int o = 0; o < 4; ++o) {
-      int ci = map_index(f - 2 + o, nx, S.bcx);
+      int io = f - 2 + o;
+      int ci = map_index(io, nx, S.bcx);
       double w[4], wx[4];
-      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, j, ci)]; wx[v] = Wx[cidx(S, v, j, ci)]; }
-      if (is_mirror(f - 2 + o, nx, S.bcx)) mirror_cell(n, 1, w, wx);
+      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, jm, ci)]; wx[v] = Wx[cidx(S, v, jm, ci)]; }
+      if (is_mirror(io, nx, S.bcx)) mirror_cell(n, 1, w, wx);
+      if (is_iso(io, nx, S.bcx)) iso_ghost(S, 1, io < 0 ? 0 : 1, true, w, wx);
+      if (k >= ny) iso_ghost(S, 2, j < 0 ? 0 : 1, false, w, wx);
       for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dx * wx[v]; }
     }
     if (!normal_recon(S, in8, S.dx, rx[idx])) {
@@ -920,6 +980,9 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       ok = false;
     }
   }
+  // the x-face row of tangential index jt (ghost rows of isothermal walls stored after the
+  // interior ones)
+  auto xrow = [&](int jt) { return jt >= 0 && jt < ny ? jt : (jt < 0 ? ny + 2 + jt : ny + 2 + (jt - ny)); };
   fx.assign((size_t)(nx + 1) * ny, FaceOut());
 #pragma omp parallel for schedule(static)
   for (long idx = 0; idx < (long)(nx + 1) * ny; ++idx) {
@@ -941,8 +1004,10 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
         const FaceRecon* rr[5];
         FaceRecon mir[5];
         for (int t = 0; t < 5; ++t) {
-          rr[t] = &rx[(size_t)map_index(j - 2 + t, ny, S.bcy) * (nx + 1) + f];
-          if (is_mirror(j - 2 + t, ny, S.bcy)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
+          const int jt = j - 2 + t;
+          if (is_iso(jt, ny, S.bcy)) { rr[t] = &rx[(size_t)xrow(jt) * (nx + 1) + f]; continue; }
+          rr[t] = &rx[(size_t)map_index(jt, ny, S.bcy) * (nx + 1) + f];
+          if (is_mirror(jt, ny, S.bcy)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
         }
         tangential_point(S, rr, g, S.dy, pin);
       }
@@ -962,16 +1027,25 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
 
   // ---- y faces: face f at y_{f-1/2}, f = 0..ny, columns i = 0..nx-1.  Evaluated in the
   // local frame where the face normal is the first axis (velocity components swapped). ----
-  std::vector<FaceRecon> ry((size_t)(ny + 1) * nx);
+  // With isothermal walls in x (R25) the y faces of the four ghost columns i = -2, -1, nx,
+  // nx + 1 are reconstructed as well, from ghost cells (the x wall's map first).
+  const bool isox = S.bcx == 3;
+  const int ncy = isox ? nx + 4 : nx;
+  std::vector<FaceRecon> ry((size_t)(ny + 1) * ncy);
 #pragma omp parallel for schedule(static)
-  for (long idx = 0; idx < (long)(ny + 1) * nx; ++idx) {
-    int i = (int)(idx % nx), f = (int)(idx / nx);
+  for (long idx = 0; idx < (long)(ny + 1) * ncy; ++idx) {
+    int k = (int)(idx % ncy), f = (int)(idx / ncy);
+    int i = k < nx ? k : (k - nx < 2 ? k - nx - 2 : nx + (k - nx - 2));
+    int im = map_index(i, nx, S.bcx);
     double in8[4][8];
     for (int o = 0; o < 4; ++o) {
-      int cj = map_index(f - 2 + o, ny, S.bcy);
+      int jo = f - 2 + o;
+      int cj = map_index(jo, ny, S.bcy);
       double w[4], wy[4];
-      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, cj, i)]; wy[v] = Wy[cidx(S, v, cj, i)]; }
-      if (is_mirror(f - 2 + o, ny, S.bcy)) mirror_cell(n, 2, w, wy);
+      for (int v = 0; v < n; ++v) { w[v] = W[cidx(S, v, cj, im)]; wy[v] = Wy[cidx(S, v, cj, im)]; }
+      if (k >= nx) iso_ghost(S, 1, i < 0 ? 0 : 1, false, w, wy);
+      if (is_mirror(jo, ny, S.bcy)) mirror_cell(n, 2, w, wy);
+      if (is_iso(jo, ny, S.bcy)) iso_ghost(S, 2, jo < 0 ? 0 : 1, true, w, wy);
       swapuv(dim, w); swapuv(dim, wy);
       for (int v = 0; v < n; ++v) { in8[v][o] = w[v]; in8[v][4 + o] = S.dy * wy[v]; }
     }
@@ -980,6 +1054,7 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       ok = false;
     }
   }
+  auto ycol = [&](int it) { return it >= 0 && it < nx ? it : (it < 0 ? nx + 2 + it : nx + 2 + (it - nx)); };
   fy.assign((size_t)(ny + 1) * nx, FaceOut());
 #pragma omp parallel for schedule(static)
   for (long idx = 0; idx < (long)(ny + 1) * nx; ++idx) {
@@ -992,8 +1067,10 @@ bool eval_faces(Solver& S, const std::vector<double>& W, const std::vector<doubl
       const FaceRecon* rr[5];
       FaceRecon mir[5];
       for (int t = 0; t < 5; ++t) {
-        rr[t] = &ry[(size_t)f * nx + map_index(i - 2 + t, nx, S.bcx)];
-        if (is_mirror(i - 2 + t, nx, S.bcx)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
+        const int it = i - 2 + t;
+        if (is_iso(it, nx, S.bcx)) { rr[t] = &ry[(size_t)f * ncy + ycol(it)]; continue; }
+        rr[t] = &ry[(size_t)f * ncy + map_index(it, nx, S.bcx)];
+        if (is_mirror(it, nx, S.bcx)) { mir[t] = mirror_tangential(*rr[t]); rr[t] = &mir[t]; }
       }
       tangential_point(S, rr, g, S.dx, pin);
       PointOut po;
@@ -1204,7 +1281,7 @@ void* orc_create(int nx, int ny, double gamma, double mu, double Pr, int order, 
   if (recon != 0 && recon != 1) return nullptr;
   if (!(gamma > 1.0) || !(mu >= 0.0) || !(Pr > 0.0)) return nullptr;
   if (!(x1 > x0) || (ny > 1 && !(y1 > y0))) return nullptr;
-  if (bc_x < 0 || bc_x > 2 || bc_y < 0 || bc_y > 2) return nullptr;
+  if (bc_x < 0 || bc_x > 3 || bc_y < 0 || bc_y > 3) return nullptr;
   Solver* S = new Solver();
   S->nx = nx; S->ny = ny; S->dim = ny > 1 ? 2 : 1; S->nv = S->dim + 2;
   S->order = order; S->recon = recon; S->bcx = bc_x; S->bcy = bc_y;
@@ -1224,6 +1301,21 @@ void orc_destroy(void* h) { delete static_cast<Solver*>(h); }
 void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; }
 // R8 option: 0 = WENO-Z in characteristic variables (default), 1 = component-wise.
 void orc_set_char_mode(void* h, int m) { static_cast<Solver*>(h)->char_mode = m; }
+// Isothermal walls (bc 3, R25): T[4] wall temperatures p/rho and u[4] tangential wall
+// velocities at x0, x1, y0, y1.
+void orc_set_walls(void* h, const double* T, const double* u) {
+  Solver* S = static_cast<Solver*>(h);
+  for (int k = 0; k < 4; ++k) { S->wall_T[k] = T[k]; S->wall_u[k] = u[k]; }
+}
+// The ghost of an isothermal wall (R25) for the tests: w, d (nv values each) replaced by the
+// ghost's; axis 1 = x, 2 = y; side 0 low, 1 high; normal != 0: d is the derivative across the
+// wall.  Returns 0, or -1 for a bad argument.
+int orc_iso_ghost(void* h, int axis, int side, int normal, double* w, double* d) {
+  Solver* S = static_cast<Solver*>(h);
+  if (axis < 1 || axis > S->dim || side < 0 || side > 1) return -1;
+  iso_ghost(*S, axis, side, normal != 0, w, d);
+  return 0;
+}
 // R9 option: 0 = tangential quartic for every face quantity (default), 1 = tangential WENO-Z
 // for the non-equilibrium states (WENO-Z schemes only).
 void orc_set_tan_mode(void* h, int m) { static_cast<Solver*>(h)->tan_mode = m; }

@@ -79,7 +79,7 @@ class State:
     x1: float
     y0: float = 0.0
     y1: float = 1.0
-    bc_x: int = 0          # 0 periodic, 1 transmissive, 2 reflecting wall
+    bc_x: int = 0          # 0 periodic, 1 transmissive, 2 reflecting wall, 3 isothermal wall
     bc_y: int = 0
     mu: float = 0.0
     Pr: float = 1.0
@@ -88,6 +88,10 @@ class State:
     t_end: float = 0.0
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # isothermal no-slip walls (bc 3): temperature p/rho and tangential velocity of the walls
+    # at x0, x1, y0, y1
+    wall_T: tuple = (1.0, 1.0, 1.0, 1.0)
+    wall_u: tuple = (0.0, 0.0, 0.0, 0.0)
 
     @property
     def dx(self):
@@ -415,6 +419,82 @@ def shear_layer_2d(n: int, seed: int = 0, gamma: float = 1.4, mu: float = 1e-4, 
     del J, I
     return State(W, Wx, Wy, nx, ny, gamma, 0.0, 1.0, 0.0, 1.0, 0, 0, mu=mu, Pr=Pr, order=order,
                  recon=recon, t_end=1.0, name="shear_layer_2d")
+
+
+# ---------------------------------------------------------------------------
+# Flows between isothermal no-slip walls
+# ---------------------------------------------------------------------------
+def couette_profile(y, U, T0, Pr, gamma):
+    """Plane Couette flow between walls at y = 0 (at rest) and y = 1 (moving at U), both at
+    temperature T0 = p/rho, with constant viscosity and Prandtl number: u = U y, uniform p,
+    and the viscous heating k T'' + mu u'^2 = 0 with k = mu c_p / Pr, c_p = gamma/(gamma - 1)
+    (gas constant 1), i.e. T = T0 + Pr U^2 / (2 c_p) y (1 - y).  Returns (u, T)."""
+    cp = gamma / (gamma - 1.0)
+    return U * y, T0 + Pr * U * U / (2.0 * cp) * y * (1.0 - y)
+
+
+def couette_2d(ny: int, nx: int = 5, U: float = 0.2, mu: float = 0.02, Pr: float = 0.72,
+               gamma: float = 1.4, order: int = 8, recon: int = 0, walls: str = "y") -> State:
+    """Steady plane Couette flow (couette_profile, p = 1/gamma, T0 = 1/gamma) as the initial
+    state.  walls "y": periodic in x on [0, nx/ny], isothermal walls at y = 0, 1, the upper
+    one moving at U along x.  walls "x": the same flow turned by a quarter: walls at x = 0, 1,
+    the one at x = 1 moving at U along y, periodic in y on [0, nx/ny] (nx, ny swap roles)."""
+    T0 = 1.0 / gamma
+
+    def pt(s):
+        u, T = couette_profile(s, U, T0, Pr, gamma)
+        return u, T
+
+    if walls == "y":
+        def pfn(x, y):
+            u, T = pt(y)
+            p = np.full(np.broadcast(x, y).shape, 1.0 / gamma)
+            return conservative_2d(p / T + 0 * x, u + 0 * x, 0.0 * (x + y), p, gamma)
+        W, Wx, Wy = _cell_state_2d(pfn, nx, ny, 0.0, nx / ny, 0.0, 1.0, gamma)
+        return State(W, Wx, Wy, nx, ny, gamma, 0.0, nx / ny, 0.0, 1.0, 0, 3, mu=mu, Pr=Pr,
+                     order=order, recon=recon, t_end=5.0, name="couette_2d",
+                     meta=dict(U=U, T0=T0), wall_T=(T0,) * 4, wall_u=(0.0, 0.0, 0.0, U))
+
+    def pfn(x, y):
+        v, T = pt(x)
+        p = np.full(np.broadcast(x, y).shape, 1.0 / gamma)
+        return conservative_2d(p / T + 0 * y, 0.0 * (x + y), v + 0 * y, p, gamma)
+    W, Wx, Wy = _cell_state_2d(pfn, ny, nx, 0.0, 1.0, 0.0, nx / ny, gamma)
+    return State(W, Wx, Wy, ny, nx, gamma, 0.0, 1.0, 0.0, nx / ny, 3, 0, mu=mu, Pr=Pr,
+                 order=order, recon=recon, t_end=5.0, name="couette_2d_x",
+                 meta=dict(U=U, T0=T0), wall_T=(T0,) * 4, wall_u=(0.0, U, 0.0, 0.0))
+
+
+def heat_conduction_1d(N: int, TL: float = 0.6, TR: float = 0.8, mu: float = 0.02,
+                       Pr: float = 0.72, gamma: float = 1.4, order: int = 8,
+                       recon: int = 0) -> State:
+    """Gas at rest between isothermal walls at x = 0 (temperature TL = p/rho) and x = 1 (TR),
+    in its steady state with constant conductivity: T linear, p = 1/gamma, rho = p/T."""
+    p = 1.0 / gamma
+
+    def f(x):
+        T = TL + (TR - TL) * x
+        return p / T, 0.0 * x, np.full_like(x, p)
+    W, Wx = cell_state_1d([(0.0, 1.0, f)], N, 0.0, 1.0, gamma)
+    return State(W, Wx, None, N, 1, gamma, 0.0, 1.0, bc_x=3, mu=mu, Pr=Pr, order=order,
+                 recon=recon, t_end=5.0, name="heat_conduction_1d", meta=dict(TL=TL, TR=TR),
+                 wall_T=(TL, TR, 1.0, 1.0))
+
+
+def lid_cavity_2d(n: int, U: float = 0.15, Re: float = 1000.0, gamma: float = 1.4,
+                  Pr: float = 0.72, order: int = 8, recon: int = 1) -> State:
+    """Lid-driven cavity on [0,1]^2 (Sec. 5): gas at rest, rho = 1, p = 1/gamma (T = p/rho on
+    every wall), isothermal no-slip walls on all four sides, the upper one moving at U along
+    x; mu = rho U L / Re."""
+    T0 = 1.0 / gamma
+
+    def pfn(x, y):
+        one = np.ones(np.broadcast(x, y).shape)
+        return conservative_2d(one, 0.0 * one, 0.0 * one, one / gamma, gamma)
+    W, Wx, Wy = _cell_state_2d(pfn, n, n, 0.0, 1.0, 0.0, 1.0, gamma)
+    return State(W, Wx, Wy, n, n, gamma, 0.0, 1.0, 0.0, 1.0, 3, 3, mu=U / Re, Pr=Pr,
+                 order=order, recon=recon, t_end=1.0, name="lid_cavity_2d",
+                 meta=dict(U=U, Re=Re), wall_T=(T0,) * 4, wall_u=(0.0, 0.0, 0.0, U))
 
 
 # ---------------------------------------------------------------------------

@@ -177,4 +177,4 @@ def test_walls_conserve_mass_and_energy(make):
 
 def test_oracle_rejects_unknown_boundary():
     with pytest.raises(ValueError):
-        oracle.Solver(10, 1, bc_x=3)
+        oracle.Solver(10, 1, bc_x=4)
