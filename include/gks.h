@@ -50,8 +50,14 @@ enum { GKS_RECON_LINEAR = 0, GKS_RECON_WENOZ = 1 };
  * GKS_BC_REFLECTING, a solid wall (the reflecting boundary of the blast-wave and
  * double-Mach tests of Sec. 5): ghost k outside the wall is the mirror image of cell k
  * inside, with the momentum normal to the wall negated and, of the gradient normal to the
- * wall, every component but that momentum's negated. */
-enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_REFLECTING = 2 };
+ * wall, every component but that momentum's negated;
+ * GKS_BC_ISOTHERMAL, an isothermal no-slip wall (the walls of the lid-driven cavity of Sec.
+ * 5), FP64 form only: ghost k carries the primitive state of cell k inside with the same
+ * pressure, the normal velocity negated, the tangential velocity reflected through the
+ * wall's (u_t -> 2 u_w - u_t) and the temperature p/rho through the wall's (T -> 2 T_w - T),
+ * density p/T, and the derivatives of that ghost field; wall temperatures and velocities in
+ * gks_opts.wall_T / wall_u. */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_REFLECTING = 2, GKS_BC_ISOTHERMAL = 3 };
 /* GKS_PREC_FP64: every step in FP64.
  * GKS_PREC_FP32_BULK: reconstruction, WENO-Z and gas-kinetic arithmetic of the face sweeps in
  * FP32 on differences from a reference cell (the state mirrored as float hi/lo pairs); the
@@ -61,7 +67,8 @@ enum { GKS_PREC_FP64 = 0, GKS_PREC_FP32_BULK = 1 };
 
 typedef struct gks_opts {
   double x0, x1, y0, y1;   /* domain; dx = (x1 - x0)/nx, dy = (y1 - y0)/ny */
-  int bc_x, bc_y;          /* GKS_BC_PERIODIC, GKS_BC_TRANSMISSIVE or GKS_BC_REFLECTING */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC, GKS_BC_TRANSMISSIVE, GKS_BC_REFLECTING or
+                              GKS_BC_ISOTHERMAL */
   int precision;           /* GKS_PREC_FP64 or GKS_PREC_FP32_BULK */
   double weno_eps;         /* epsilon of the WENO-Z weights, Eq. (WENO-Z-w); default 1e-6 (the
                               paper prints none; 1e-6 reproduces Tables 3-4 of Sec. 4.1) */
@@ -80,10 +87,17 @@ typedef struct gks_opts {
                               for the initial non-equilibrium states (their values, tangential
                               and normal derivatives), as Sec. 3.3 carried across the face:
                               keeps a discontinuity aligned with the grid physical */
+  double wall_T[4];        /* GKS_BC_ISOTHERMAL walls at x0, x1, y0, y1: temperature p/rho
+                              (finite, > 0; all four are checked when any wall is isothermal) */
+  double wall_u[4];        /* and the wall's velocity along itself (x walls: the y velocity;
+                              y walls: the x velocity; unused in 1D).  A moving isothermal
+                              wall may not meet a GKS_BC_REFLECTING one (GKS_EINVAL): the
+                              mirror image of a moving wall moves the other way */
 } gks_opts;
 
 /* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-6,
- * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL, tan_mode 0. */
+ * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL, tan_mode 0, wall_T 1,
+ * wall_u 0. */
 void gks_default_opts(gks_opts* o);
 
 /* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio

@@ -82,6 +82,7 @@ def lib():
             L.orc_set_char_mode.argtypes = [c_void, c_int]
             L.orc_set_tan_mode.argtypes = [c_void, c_int]
             L.orc_set_walls.argtypes = [c_void, dp, dp]
+            L.orc_set_walls.restype = c_int
             L.orc_iso_ghost.argtypes = [c_void, c_int, c_int, c_int, dp, dp]
             L.orc_tan_weno.argtypes = [dp, c_int, c_int, c_double, dp]
             L.orc_tan_weno.restype = c_double
@@ -248,7 +249,10 @@ class Solver:
         lib().orc_set_tan_mode(self._h, int(tan_mode))
         wt = np.ascontiguousarray(wall_T, dtype=np.float64)
         wu = np.ascontiguousarray(wall_u, dtype=np.float64)
-        lib().orc_set_walls(self._h, _p(wt), _p(wu))
+        if lib().orc_set_walls(self._h, _p(wt), _p(wu)) != 0:
+            lib().orc_destroy(self._h)
+            self._h = None
+            raise ValueError("a moving isothermal wall meets a reflecting wall")
 
     def __del__(self):
         h = getattr(self, "_h", None)

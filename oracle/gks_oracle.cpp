@@ -77,7 +77,8 @@
 //       mirror: along the wall normal the pressure's changes sign and the velocity's and
 //       temperature's keep theirs; along the wall the opposite.  Cell
 //       averages are treated as point values in this map (the boundary is low order).  A cell
-//       beyond two walls (a corner) takes the x wall's map first, then the y wall's.
+//       beyond two walls (a corner) takes the x wall's map first, then the y wall's.  A
+//       moving isothermal wall does not meet a reflecting wall (rejected).
 //   R23 the equilibrium state g0 takes its value from the collision of the two initial
 //       states, W0 = int_{u>0} psi g_l + int_{u<0} psi g_r (identical to the linear
 //       reconstruction when the scheme is linear), and its derivatives from the compact
@@ -1302,10 +1303,16 @@ void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; 
 // R8 option: 0 = WENO-Z in characteristic variables (default), 1 = component-wise.
 void orc_set_char_mode(void* h, int m) { static_cast<Solver*>(h)->char_mode = m; }
 // Isothermal walls (bc 3, R25): T[4] wall temperatures p/rho and u[4] tangential wall
-// velocities at x0, x1, y0, y1.
-void orc_set_walls(void* h, const double* T, const double* u) {
+// velocities at x0, x1, y0, y1.  Returns -1 (nothing set) when a moving isothermal wall meets
+// a reflecting one: the mirror image of a moving wall moves the other way, so the corner
+// ghosts would depend on the order of the two maps.
+int orc_set_walls(void* h, const double* T, const double* u) {
   Solver* S = static_cast<Solver*>(h);
+  if (S->dim == 2 && ((S->bcx == 2 && S->bcy == 3 && (u[2] != 0.0 || u[3] != 0.0)) ||
+                      (S->bcy == 2 && S->bcx == 3 && (u[0] != 0.0 || u[1] != 0.0))))
+    return -1;
   for (int k = 0; k < 4; ++k) { S->wall_T[k] = T[k]; S->wall_u[k] = u[k]; }
+  return 0;
 }
 // The ghost of an isothermal wall (R25) for the tests: w, d (nv values each) replaced by the
 // ghost's; axis 1 = x, 2 = y; side 0 low, 1 high; normal != 0: d is the derivative across the

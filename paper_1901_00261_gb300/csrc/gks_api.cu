@@ -126,6 +126,7 @@ int enqueue_step(gks_ctx* c, cudaEvent_t* ev = nullptr, double* state = nullptr)
   fa.dtp = c->d_dt; fa.status = c->d_status;
   fa.nx = c->nx; fa.ny = c->ny; fa.bcx = c->o.bc_x; fa.bcy = c->o.bc_y;
   fa.P = c->P;
+  for (int k = 0; k < 4; ++k) { fa.wallT[k] = c->o.wall_T[k]; fa.wallU[k] = c->o.wall_u[k]; }
   const bool visc = c->P.mu > 0.0 || c->P.tau_mode == 1;
   const long L = state_len(c);
   gks::UpdateArgs ua;
@@ -209,6 +210,7 @@ void gks_default_opts(gks_opts* o) {
   o->tau_mode = 0;
   o->tan_mode = 0;
   o->stream = nullptr;
+  for (int k = 0; k < 4; ++k) { o->wall_T[k] = 1.0; o->wall_u[k] = 0.0; }
 }
 
 const char* gks_last_error(void) { return g_err.c_str(); }
@@ -226,7 +228,20 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   gks_opts o;
   if (opts) o = *opts; else gks_default_opts(&o);
   if (!(o.x1 > o.x0) || (ny > 1 && !(o.y1 > o.y0))) { fail(GKS_EINVAL, "empty domain%s"); return nullptr; }
-  if (o.bc_x < 0 || o.bc_x > 2 || o.bc_y < 0 || o.bc_y > 2) { fail(GKS_EINVAL, "bc must be 0, 1 or 2%s"); return nullptr; }
+  if (o.bc_x < 0 || o.bc_x > 3 || o.bc_y < 0 || o.bc_y > 3) { fail(GKS_EINVAL, "bc must be 0, 1, 2 or 3%s"); return nullptr; }
+  if (o.bc_x == GKS_BC_ISOTHERMAL || (ny > 1 && o.bc_y == GKS_BC_ISOTHERMAL)) {
+    if (o.precision != GKS_PREC_FP64) { fail(GKS_EINVAL, "isothermal walls run in the FP64 form only%s"); return nullptr; }
+    for (int k = 0; k < 4; ++k)
+      if (!(o.wall_T[k] > 0.0) || !std::isfinite(o.wall_T[k]) || !std::isfinite(o.wall_u[k])) {
+        fail(GKS_EINVAL, "wall_T must be finite and > 0, wall_u finite%s"); return nullptr;
+      }
+    // the mirror image of a moving wall moves the other way: a corner of a moving isothermal
+    // wall and a reflecting one has no consistent ghost
+    if (ny > 1 && ((o.bc_x == GKS_BC_REFLECTING && (o.wall_u[2] != 0.0 || o.wall_u[3] != 0.0)) ||
+                   (o.bc_y == GKS_BC_REFLECTING && (o.wall_u[0] != 0.0 || o.wall_u[1] != 0.0)))) {
+      fail(GKS_EINVAL, "a moving isothermal wall cannot meet a reflecting wall%s"); return nullptr;
+    }
+  }
   if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_FP32_BULK) { fail(GKS_EINVAL, "unsupported precision%s"); return nullptr; }
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
   if (o.tau_mode != 0 && o.tau_mode != 1) { fail(GKS_EINVAL, "tau_mode must be 0 or 1%s"); return nullptr; }

@@ -66,6 +66,10 @@ __global__ void __launch_bounds__(128) faces_1d_kernel(FaceArgs a) {
 #pragma unroll
     for (int v = 0; v < N; ++v) { w[v] = a.W[v * ncell + c]; g[v] = a.Wn[v * ncell + c]; }
     if (a.bcx == 2) mirror_ghost<1, 0, R>(w, nullptr, g, beyond_wall(f - 2 + o, a.nx, 2), false);
+    if (beyond_iso(f - 2 + o, a.nx, a.bcx)) {
+      const int side = f - 2 + o < 0 ? 0 : 1;
+      iso_ghost<1>(w, g, 0, true, a.wallT[side], a.wallU[side], a.P.gamma);
+    }
 #pragma unroll
     for (int v = 0; v < N; ++v) { in[v][o] = w[v]; in[v][4 + o] = a.dn * g[v]; }
   }
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
   // grids skip the mirror signs)
   const int bcn = DIR == 0 ? a.bcx : a.bcy, bct = DIR == 0 ? a.bcy : a.bcx;
   const bool walls = (bcn == 2) | (bct == 2);
+  const bool iso = (bcn == 3) | (bct == 3);
   for (int s = tid; s < T::NS; s += nthreads) {
     int sa = s % T::SA, sb = s / T::SA;
     int fn, ctr;   // normal face index, tangential cell index (before mapping)
@@ -145,6 +150,18 @@ __global__ void __launch_bounds__(TA * TB) faces_2d_kernel(FaceArgs a) {
         if (walls)
           mirror_ghost<2, DIR, double>(w, nullptr, g, beyond_wall(fn - 2 + o, nnc, bcn),
                                        beyond_wall(ctr, ntc, bct));
+        if (iso) {
+          // isothermal walls: the x wall's map first, then the y wall's (a corner cell)
+          const int ix = DIR == 0 ? fn - 2 + o : ctr, iy = DIR == 0 ? ctr : fn - 2 + o;
+          if (beyond_iso(ix, a.nx, a.bcx)) {
+            const int k = ix < 0 ? 0 : 1;
+            iso_ghost<2>(w, g, 0, DIR == 0, a.wallT[k], a.wallU[k], a.P.gamma);
+          }
+          if (beyond_iso(iy, a.ny, a.bcy)) {
+            const int k = iy < 0 ? 2 : 3;
+            iso_ghost<2>(w, g, 1, DIR == 1, a.wallT[k], a.wallU[k], a.P.gamma);
+          }
+        }
         if (DIR == 1) { swap_uv<2>(w); swap_uv<2>(g); }
 #pragma unroll
         for (int v = 0; v < N; ++v) { in[v][o] = w[v]; in[v][4 + o] = a.dn * g[v]; }

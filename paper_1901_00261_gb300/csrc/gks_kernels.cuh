@@ -59,10 +59,11 @@ struct FaceArgs {
   const double* dtp;   // device scalar dt
   unsigned int* status;
   int nx, ny;          // cells
-  int bcx, bcy;        // 0 periodic, 1 transmissive
+  int bcx, bcy;        // 0 periodic, 1 transmissive, 2 reflecting wall, 3 isothermal wall
   double dn, dtan;     // cell size along the normal / tangential direction
   int stage;           // 1 or 2
   PhysParams P;
+  double wallT[4], wallU[4];   // isothermal walls at x0, x1, y0, y1: p/rho, tangential velocity
 };
 
 // Cell update after the face sweeps of a stage.

@@ -6,10 +6,11 @@
 namespace gks {
 
 // Cell holding the data of index i of a line of n cells.  bc 0 periodic; bc 1 transmissive
-// (the boundary cell); bc 2 reflecting wall: the mirror image across the wall (index -1 is
-// cell 0, index n is cell n - 1), whose signs mirror_ghost applies.  Indices further out
-// than n, which only the overhang of a tile beyond the grid reaches and no face uses, are
-// clamped into the grid.  WALLS = false: a kernel launched only for bc 0 and 1.
+// (the boundary cell); bc 2 reflecting wall and bc 3 isothermal wall: the mirror image across
+// the wall (index -1 is cell 0, index n is cell n - 1), which mirror_ghost (bc 2) or
+// iso_ghost (bc 3) turns into the ghost.  Indices further out than n, which only the
+// overhang of a tile beyond the grid reaches and no face uses, are clamped into the grid.
+// WALLS = false: a kernel launched only for bc 0 and 1.
 template <bool WALLS = true>
 __device__ __forceinline__ int map_index(int i, int n, int bc) {
   if (bc == 0) {
@@ -19,13 +20,56 @@ __device__ __forceinline__ int map_index(int i, int n, int bc) {
     else if (i < 0) { i += n; if (i < 0) { i %= n; if (i < 0) i += n; } }
     return i;
   }
-  if (WALLS && bc == 2) { if (i < 0) i = -1 - i; else if (i >= n) i = 2 * n - 1 - i; }
+  if (WALLS && bc >= 2) { if (i < 0) i = -1 - i; else if (i >= n) i = 2 * n - 1 - i; }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
 // True when index i of a line of n cells lies beyond a reflecting wall.
 __device__ __forceinline__ bool beyond_wall(int i, int n, int bc) {
   return bc == 2 && (unsigned)i >= (unsigned)n;
+}
+
+// True when index i of a line of n cells lies beyond an isothermal wall.
+__device__ __forceinline__ bool beyond_iso(int i, int n, int bc) {
+  return bc == 3 && (unsigned)i >= (unsigned)n;
+}
+
+// Ghost of a cell beyond an isothermal no-slip wall normal to axis `axis` (0 = x, 1 = y):
+// the mirror cell's primitive state with the same pressure, the normal velocity negated,
+// the tangential one reflected through the wall's (u_t -> 2 u_w - u_t) and the temperature
+// p/rho reflected through the wall's (T -> 2 T_w - T), density p/T.  w: conservative values
+// (global frame), replaced by the ghost's; g: their derivatives along the stencil, which
+// crosses the wall when `normal` (then an even quantity's derivative changes sign) and runs
+// along it otherwise; replaced by the derivatives of the ghost field.
+template <int DIM>
+__device__ __forceinline__ void iso_ghost(double* w, double* g, int axis, bool normal, double Tw,
+                                          double uw, double gamma) {
+  const int N = DIM + 2;
+  const double g1 = gamma - 1.0, irho = 1.0 / w[0];
+  const double rho = w[0];
+  const double u0 = w[1] * irho, u1 = DIM == 2 ? w[2] * irho : 0.0;
+  const double ke = 0.5 * (u0 * u0 + u1 * u1);
+  const double p = g1 * (w[N - 1] - rho * ke), T = p * irho;
+  const double dr = g[0];
+  const double du0 = (g[1] - u0 * dr) * irho, du1 = DIM == 2 ? (g[2] - u1 * dr) * irho : 0.0;
+  const double dp = g1 * (g[N - 1] - dr * ke - rho * (u0 * du0 + u1 * du1));
+  const double dT = (dp - T * dr) * irho;
+  const double sn = normal ? -1.0 : 1.0;   // the sign the map gives an even quantity's slope
+  // ghost velocity: the normal component negated, the tangential reflected through uw
+  double v0, v1, dv0, dv1;
+  if (axis == 0) { v0 = -u0; dv0 = -sn * du0; v1 = 2.0 * uw - u1; dv1 = -sn * du1; }
+  else { v1 = -u1; dv1 = -sn * du1; v0 = 2.0 * uw - u0; dv0 = -sn * du0; }
+  if (DIM == 1) { v1 = 0.0; dv1 = 0.0; }
+  const double Tg = 2.0 * Tw - T, dTg = -sn * dT;
+  const double pg = p, dpg = sn * dp;
+  const double itg = 1.0 / Tg;
+  const double rg = pg * itg, drg = (dpg - rg * dTg) * itg;
+  const double keg = 0.5 * (v0 * v0 + v1 * v1), dkeg = v0 * dv0 + v1 * dv1;
+  w[0] = rg; g[0] = drg;
+  w[1] = rg * v0; g[1] = drg * v0 + rg * dv0;
+  if (DIM == 2) { w[2] = rg * v1; g[2] = drg * v1 + rg * dv1; }
+  w[N - 1] = pg / g1 + rg * keg;
+  g[N - 1] = dpg / g1 + drg * keg + rg * dkeg;
 }
 
 // Mirror image of a cell beyond a reflecting wall (conservative variables in the global

@@ -17,7 +17,7 @@ from . import build as _build
 GKS_OK, GKS_EINVAL, GKS_ECUDA, GKS_ENOMEM, GKS_ENONPHYSICAL, GKS_ETIMEOUT = 0, -1, -2, -3, -4, -5
 RECON_LINEAR, RECON_WENOZ = 0, 1
 PREC_FP64, PREC_FP32_BULK = 0, 1
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_ISOTHERMAL = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int),
                 ("tau_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p),
-                ("tan_mode", ctypes.c_int)]
+                ("tan_mode", ctypes.c_int),
+                ("wall_T", ctypes.c_double * 4), ("wall_u", ctypes.c_double * 4)]
 
 
 # Every symbol include/gks.h declares, with (restype, argtypes).
@@ -156,7 +157,8 @@ class Solver:
                  y0: float = 0.0, y1: float = 1.0, bc_x: int = BC_PERIODIC, bc_y: int = BC_PERIODIC,
                  weno_eps: float = 1e-6, use_graph: bool = True, stream=None,
                  precision: int = PREC_FP64, tau_mode: int = 0, eps_tau: float = 0.01,
-                 C_tau: float = 1.0, tan_mode: int = 0):
+                 C_tau: float = 1.0, tan_mode: int = 0, wall_T=(1.0, 1.0, 1.0, 1.0),
+                 wall_u=(0.0, 0.0, 0.0, 0.0)):
         L = lib()
         o = default_opts()
         o.precision = precision
@@ -166,6 +168,8 @@ class Solver:
         o.use_graph = 1 if use_graph else 0
         o.tau_mode = tau_mode
         o.tan_mode = tan_mode
+        for k in range(4):
+            o.wall_T[k], o.wall_u[k] = float(wall_T[k]), float(wall_u[k])
         o.eps_tau, o.C_tau = eps_tau, C_tau
         o.stream = stream
         self._h = L.gks_create(nx, ny, gamma, mu, Pr, order, recon, ctypes.byref(o))
@@ -178,6 +182,8 @@ class Solver:
     @classmethod
     def from_state(cls, st, **kw):
         """Solver configured from an inputs.State (grid, BCs, physics, order, recon)."""
+        kw.setdefault("wall_T", st.wall_T)
+        kw.setdefault("wall_u", st.wall_u)
         s = cls(st.nx, st.ny, st.gamma, st.mu, st.Pr, st.order, st.recon, st.x0, st.x1,
                 st.y0, st.y1, st.bc_x, st.bc_y, **kw)
         s.set_state(st.W, st.Wx, st.Wy)

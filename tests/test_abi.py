@@ -37,6 +37,28 @@ def test_default_opts():
     o = gks.default_opts()
     assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-6, 0.01, 1.0, 1)
     assert o.tau_mode == 0 and o.stream is None and o.tan_mode == 0
+    # the last fields: a layout mismatch between the header and the binding shows here
+    assert list(o.wall_T) == [1.0] * 4 and list(o.wall_u) == [0.0] * 4
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(bc_x=4), "bc must be"),
+    (dict(bc_x=3, precision=1), "FP64 form only"),
+    (dict(bc_y=3, wall_T=(1.0, 1.0, 0.0, 1.0)), "wall_T"),
+    (dict(bc_x=3, wall_u=(0.0, float("nan"), 0.0, 0.0)), "wall_u"),
+    (dict(bc_x=2, bc_y=3, wall_u=(0.0, 0.0, 0.0, 0.1)), "reflecting"),
+])
+def test_create_rejects_invalid_walls(change, msg):
+    L = gks.lib()
+    o = gks.default_opts()
+    for k, v in change.items():
+        if k in ("wall_T", "wall_u"):
+            for i, x in enumerate(v):
+                getattr(o, k)[i] = x
+        else:
+            setattr(o, k, v)
+    assert not L.gks_create(10, 10, 1.4, 0.01, 0.72, 6, 0, ctypes.byref(o))
+    assert msg in gks.last_error()
 
 
 def test_create_rejects_invalid_tau_mode():

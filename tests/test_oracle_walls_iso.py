@@ -192,3 +192,9 @@ def test_gas_at_rest_at_the_wall_temperature_stays_at_rest():
     W0 = st.W.copy()
     W = _run(st, 0.3)[0]
     np.testing.assert_allclose(W, W0, rtol=0, atol=1e-13)
+
+
+def test_moving_isothermal_wall_meeting_a_reflecting_wall_is_rejected():
+    with pytest.raises(ValueError):
+        oracle.Solver(8, 8, bc_x=2, bc_y=3, wall_u=(0.0, 0.0, 0.0, 0.1))
+    oracle.Solver(8, 8, bc_x=2, bc_y=3, wall_u=(0.1, 0.0, 0.0, 0.0))   # the x walls' speeds are unused
