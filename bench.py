@@ -51,28 +51,27 @@ CFL = 0.3
 # ncu's executed-instruction counters (FP32-bulk form: a 1024^2 capture; FP64 form: 256^2);
 # bytes: algorithmic bytes per unit (each datum read or written once), given for the updates,
 # whose limit is memory or the FP64 pipe (the sweeps are compute-side: issue-bound, DRAM below
-# 20 %); traffic: DRAM bytes (read + write) per unit from the 1024^2 capture, scaled to a launch
-# by the units processed (the kernels stream, so traffic grows in proportion; at 1024^2 part
-# of the data stays in L2, so it reads low).  The FP64 form has no traffic figure: its 256^2
-# capture fits in L2.  winstr: executed warp-instructions per 32 units (same captures), for
+# 20 %); traffic: DRAM bytes (read + write) per unit of a full-size launch (2048^2, one-pass
+# dram__bytes capture of the benchmark's own step), scaled by the units a launch processes.
+# The FP64 form has no traffic figure: its 256^2 capture fits in L2.  winstr: executed warp-instructions per 32 units (same captures), for
 # the instruction-issue rate the sweeps are limited by (reported beside the roofline).
 KERNEL_MODEL = {
     ("linear_euler", "fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2, "winstr": 7353},
     ("linear_euler", "fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
     ("linear_euler", "fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
     ("linear_euler", "fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
-    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 157.5,
+    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 196.3,
                                                  "winstr": 2303},
-    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 160.2,
+    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 195.2,
                                                  "winstr": 2087},
     ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
-                                                "traffic": 247.6, "winstr": 408},
-    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1826.6, "f64": 4.0, "traffic": 110.8,
+                                                "traffic": 277.8, "winstr": 408},
+    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1826.6, "f64": 4.0, "traffic": 136.5,
                                                  "winstr": 1848},
-    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1750.0, "f64": 4.0, "traffic": 114.0,
+    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1750.0, "f64": 4.0, "traffic": 135.7,
                                                  "winstr": 1651},
     ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
-                                                "traffic": 342.9, "winstr": 703},
+                                                "traffic": 373.2, "winstr": 703},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face from a 1024^2 capture
     ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 11501.0, "f64": 427.0},
