@@ -189,6 +189,10 @@ int gks_probe_alu_peak(int fp64, double* flops_per_s);
  * b0 = 4 (E0(dt) - 2 E0(dt/2))/dt^2, b1 = 4 (E1(dt) - 2 E1(dt/2))/dt^2.  Synchronous;
  * GKS_EINVAL for a NULL array, n < 0, dt or a theta not finite and > 0. */
 int gks_probe_time_coefs(const double* theta, int n, double dt, double* out);
+/* The same coefficients as the single-precision form (GKS_PREC_FP32_BULK) forms them before
+ * rounding them to float: FP64 arithmetic, series truncated where the truncation falls below
+ * 1e-9 of each coefficient.  Arguments, ownership and errors as gks_probe_time_coefs. */
+int gks_probe_time_coefs_single(const double* theta, int n, double dt, double* out);
 
 /* Test probe of the FP64 reciprocal that the single-precision sweeps use for their FP64
  * reference flux (not part of the method): for host x[i] (n >= 0 entries, each positive,

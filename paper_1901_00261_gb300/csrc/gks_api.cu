@@ -424,15 +424,25 @@ int gks_steps_timed(gks_ctx* c, double dt, int nsteps, double* kernel_ms) {
   return rc;
 }
 
-int gks_probe_time_coefs(const double* theta, int n, double dt, double* out) {
+namespace {
+int probe_time_coefs_checked(const double* theta, int n, double dt, double* out, bool single) {
   if (!theta || !out || n < 0) return fail(GKS_EINVAL, "NULL argument or n < 0%s");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(GKS_EINVAL, "dt must be finite and > 0%s");
   for (int i = 0; i < n; ++i)
     if (!(theta[i] > 0.0) || !std::isfinite(theta[i])) return fail(GKS_EINVAL, "theta must be finite and > 0%s");
   if (n == 0) return GKS_OK;
-  cudaError_t e = gks::probe_time_coefs(theta, n, dt, out);
+  cudaError_t e = gks::probe_time_coefs(theta, n, dt, out, single);
   if (e != cudaSuccess) return cuda_fail(e, "time coefficient probe");
   return GKS_OK;
+}
+}  // namespace
+
+int gks_probe_time_coefs(const double* theta, int n, double dt, double* out) {
+  return probe_time_coefs_checked(theta, n, dt, out, false);
+}
+
+int gks_probe_time_coefs_single(const double* theta, int n, double dt, double* out) {
+  return probe_time_coefs_checked(theta, n, dt, out, true);
 }
 
 int gks_probe_rcp64(const double* x, int n, double* out) {

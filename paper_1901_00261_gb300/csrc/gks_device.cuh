@@ -382,6 +382,11 @@ __device__ __forceinline__ void time_series(double x, double& pa, double& pb, do
 // Arguments in terms of theta = tau/dt and x = (dt/2)/tau = 1/(2 theta) (both formed by the
 // caller in its arithmetic type; the cancellation is inside the formulas below, which run in
 // FP64): a0 = theta S (2 + S), b0 = -4 theta S^2 / dt, a1 = theta^2 dt pa, b1 = 4 theta^2 pb.
+// SINGLE: the coefficients are rounded to float by the caller (the single-precision form),
+// so the series stop where their truncation falls below 1e-9 of the result itself (k = 10,
+// 11, 14 for x < 1/8, 1/4, 1/2; 3.4e-10 at most, measured with 50-digit arithmetic), far
+// under the float rounding that follows; the arithmetic stays FP64 (the cancellation).
+template <bool SINGLE = false>
 __device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt) {
   TimeCoef T;
   double S;        // 1 - e^{-x}
@@ -390,9 +395,9 @@ __device__ __forceinline__ TimeCoef time_coefs(double theta, double x, double dt
     // the three series, by Horner's rule in x in lockstep (x^2, resp. x, factored out),
     // truncated after the last term that reaches 1e-19 of the magnitudes above: k = 15 for
     // x < 1/8, 17 for x < 1/4, 21 for x < 1/2 (fewer dependent FP64 steps for small x)
-    if (x < 0.125) time_series<15>(x, pa, pb, S);
-    else if (x < 0.25) time_series<17>(x, pa, pb, S);
-    else time_series<21>(x, pa, pb, S);
+    if (x < 0.125) time_series<SINGLE ? 10 : 15>(x, pa, pb, S);
+    else if (x < 0.25) time_series<SINGLE ? 11 : 17>(x, pa, pb, S);
+    else time_series<SINGLE ? 14 : 21>(x, pa, pb, S);
   } else {
     // for x > 40, e^{-x} < 2^-57 and 1 - e^{-x} rounds to 1: S = 1 and e^{-x} = 0 exactly
     S = x > 40.0 ? 1.0 : -expm1(-x);
@@ -677,7 +682,7 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
       // theta = tau_n / dt (Sec. 4: mu/p, or eps dt, plus C |pl - pr| / (pl + pr) dt)
       const R theta = (P.mu > 0.0 ? fdiv<R>(R(P.mu), g0.p * R(dt)) : R(P.eps_tau)) +
                       R(P.C_tau) * fabs(fdiv<R>(pl - pr, pl + pr));
-      const TimeCoef T = time_coefs((double)theta, (double)fdiv<R>(R(0.5), theta), dt);
+      const TimeCoef T = time_coefs<sizeof(R) == 4>((double)theta, (double)fdiv<R>(R(0.5), theta), dt);
       // c0 starts from minus the collisionless flux of g0 (F_Euler(W0); the bracket is not
       // part of it), formed here so that it does not depend on F being computed
       R c0[N], c1[N];

@@ -116,7 +116,7 @@ cudaError_t launch_wavespeed(const double* W, int nx, int ny, int dim, double ga
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
 cudaError_t launch_set_times(StepTimes* p, double dt, cudaStream_t s);
 cudaError_t probe_fma(int fp64, int iters, double* flops, cudaStream_t s);
-cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out);
+cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out, bool single);
 
 // Test probe: the FP32-bulk sweeps' FP64 reciprocal of host x[0..n) into host out.
 cudaError_t probe_rcp64(const double* x, int n, double* out);

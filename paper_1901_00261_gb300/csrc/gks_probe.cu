@@ -8,12 +8,14 @@
 namespace gks {
 
 // time_coefs(theta, 1/(2 theta), dt) for theta[i], as the non-equilibrium branch of the face
-// kernels forms it (FP64 path); out[4 i ..] = a0, a1, b0, b1.
+// kernels forms it (SINGLE: the single-precision form's truncation); out[4 i ..] = a0, a1, b0,
+// b1.
+template <bool SINGLE>
 __global__ void time_coefs_probe_kernel(const double* theta, int n, double dt, double* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double th = theta[i];
-  const TimeCoef T = time_coefs(th, 0.5 / th, dt);
+  const TimeCoef T = time_coefs<SINGLE>(th, 0.5 / th, dt);
   out[4 * i + 0] = T.a0;
   out[4 * i + 1] = T.a1;
   out[4 * i + 2] = T.b0;
@@ -21,14 +23,15 @@ __global__ void time_coefs_probe_kernel(const double* theta, int n, double dt, d
 }
 
 // Host arrays theta[n] and out[4 n]; synchronous.
-cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out) {
+cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out, bool single) {
   double* d_theta = nullptr;
   double* d_out = nullptr;
   cudaError_t e = cudaMalloc(&d_theta, (size_t)n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpy(d_theta, theta, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    time_coefs_probe_kernel<<<(n + 127) / 128, 128>>>(d_theta, n, dt, d_out);
+    if (single) time_coefs_probe_kernel<true><<<(n + 127) / 128, 128>>>(d_theta, n, dt, d_out);
+    else time_coefs_probe_kernel<false><<<(n + 127) / 128, 128>>>(d_theta, n, dt, d_out);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(out, d_out, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost);

@@ -66,6 +66,7 @@ SIGNATURES = {
     "gks_steps_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _DP]),
     "gks_probe_alu_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
     "gks_probe_time_coefs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
+    "gks_probe_time_coefs_single": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
     "gks_probe_rcp64": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "gks_step_1d_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -276,13 +277,14 @@ def probe_alu_peak(fp64: bool = True) -> float:
     return v.value
 
 
-def probe_time_coefs(theta, dt: float) -> np.ndarray:
+def probe_time_coefs(theta, dt: float, single: bool = False) -> np.ndarray:
     """The face kernels' FP64 time-integration coefficients (a0, a1, b0, b1) for each
-    theta = tau/dt, evaluated on the device (gks_probe_time_coefs); shape (n, 4)."""
+    theta = tau/dt, evaluated on the device (gks_probe_time_coefs, or with single the
+    single-precision form's truncation, gks_probe_time_coefs_single); shape (n, 4)."""
     th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
     out = np.zeros((th.size, 4))
-    _check(lib().gks_probe_time_coefs(th.ctypes.data_as(_DP), th.size, float(dt),
-                                      out.ctypes.data_as(_DP)))
+    fn = lib().gks_probe_time_coefs_single if single else lib().gks_probe_time_coefs
+    _check(fn(th.ctypes.data_as(_DP), th.size, float(dt), out.ctypes.data_as(_DP)))
     return out
 
 

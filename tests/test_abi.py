@@ -91,6 +91,7 @@ def test_null_context_calls_fail_cleanly():
     assert L.gks_sync(None) == gks.GKS_EINVAL
     assert L.gks_step_host_async(None, None, None, None, None, None, None, 0.1) == gks.GKS_EINVAL
     assert L.gks_probe_time_coefs(None, 1, 0.1, None) == gks.GKS_EINVAL
+    assert L.gks_probe_time_coefs_single(None, 1, 0.1, None) == gks.GKS_EINVAL
     assert L.gks_get_state(None, None, None, None) == gks.GKS_EINVAL
     L.gks_destroy(None)
 

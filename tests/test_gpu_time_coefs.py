@@ -70,6 +70,21 @@ def test_time_coefficients_match_their_definition(dt):
     assert worst < 1e-14, worst
 
 
+@pytest.mark.parametrize("dt", [1e-3, 0.25])
+def test_single_precision_time_coefficients(dt):
+    """The single-precision form's coefficients (rounded to float after this): shorter series,
+    whose truncation stays below 1e-9 of each coefficient itself (where the series branch
+    runs, dt/(2 tau) < 1/2, no coefficient changes sign), and the same closed form above."""
+    got = gks.probe_time_coefs(THETAS, dt, single=True)
+    worst = 0.0
+    for th, row in zip(THETAS, got):
+        val, scale = reference(th, dt)
+        for g, v, s in zip(row, val, scale):
+            bound = max(Decimal(1e-9) * abs(v), Decimal(1e-14) * s)
+            worst = max(worst, float(abs(Decimal(float(g)) - v) / bound))
+    assert worst < 1.0, worst
+
+
 def test_time_coefficient_probe_rejects_bad_theta():
     with pytest.raises(gks.GksError):
         gks.probe_time_coefs(np.array([1.0, 0.0]), 0.1)
