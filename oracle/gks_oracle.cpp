@@ -29,7 +29,10 @@
 // Riemann (including the random Riemann problems of the batched workload), vortex and
 // linear-acoustics solutions, the linearised Navier-Stokes decay of shear, entropy and sound
 // waves (viscosity, heat conduction with the Prandtl fix, 1D and 2D), the mirror symmetry of
-// reflecting walls and the rotational symmetry of the 2D scheme.  Whole runs of the Shu-Osher
+// reflecting walls, plane Couette flow and steady heat conduction between isothermal walls
+// (closed forms, second-order convergence), the derivatives of the isothermal ghost field
+// (finite differences), the lid-driven cavity's mirror symmetry under lid reversal, and the
+// rotational symmetry of the 2D scheme.  Whole runs of the Shu-Osher
 // problem and the double shear layer have no exact solution: for those the parity is
 // unpinned beyond conservation, positivity and the pins of their parts.
 //
