@@ -220,8 +220,10 @@ typedef struct gks_problem {
   int order, recon;        /* 6 | 8; GKS_RECON_LINEAR | GKS_RECON_WENOZ */
   double gamma, mu, Pr;    /* as in gks_create */
   double x0, x1, y0, y1;   /* domain */
-  int bc_x, bc_y;          /* GKS_BC_PERIODIC | GKS_BC_TRANSMISSIVE (reflecting walls run
-                              in the single-problem solvers only) */
+  int bc_x, bc_y;          /* GKS_BC_PERIODIC | GKS_BC_TRANSMISSIVE | GKS_BC_REFLECTING (a
+                              batch holding a walled problem runs a persistent kernel compiled
+                              with the wall signs; isothermal walls: single-problem FP64 form
+                              only) */
 } gks_problem;
 
 /* Create a batch of n problems (copied); device memory for all of them is one allocation.

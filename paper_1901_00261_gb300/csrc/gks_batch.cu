@@ -48,10 +48,13 @@ constexpr int NFPT = 3;
 inline int fpt_index(int fpt) { return fpt == 1 ? 0 : (fpt == 2 ? 1 : (fpt == 4 ? 2 : -1)); }
 
 BatchKernelFn batch_kernel_fn(int cls, int fpt) {
+  if (cls == 2)
+    return fpt == 1 ? batch_kernel_walls_fpt1() : (fpt == 2 ? batch_kernel_walls_fpt2() : batch_kernel_walls_fpt4());
   return fpt == 1 ? batch_kernel_fpt1(cls) : (fpt == 2 ? batch_kernel_fpt2(cls) : batch_kernel_fpt4(cls));
 }
 size_t batch_smem_of(int cls, int fpt) {
-  return fpt == 1 ? batch_smem_fpt1(cls) : (fpt == 2 ? batch_smem_fpt2(cls) : batch_smem_fpt4(cls));
+  const int c = cls == 2 ? 1 : cls;   // class 2 tiles are class 1's
+  return fpt == 1 ? batch_smem_fpt1(c) : (fpt == 2 ? batch_smem_fpt2(c) : batch_smem_fpt4(c));
 }
 
 }  // namespace gks
@@ -247,12 +250,13 @@ gks_batch* gks_batch_create(int n, const gks_problem* problems, void* stream) {
     if (q.order != 6 && q.order != 8) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": order must be 6 or 8"); delete B; return nullptr; }
     if (q.recon != 0 && q.recon != 1) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": recon must be 0 or 1"); delete B; return nullptr; }
     if (!(q.gamma > 1.0) || !(q.mu >= 0.0) || !(q.Pr > 0.0) || !(q.x1 > q.x0) || (q.ny > 1 && !(q.y1 > q.y0))) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": invalid physics or domain"); delete B; return nullptr; }
-    // reflecting walls run in the single-problem solvers only (the persistent kernel is
-    // compiled without the wall signs)
-    if ((q.bc_x != 0 && q.bc_x != 1) || (q.bc_y != 0 && q.bc_y != 1)) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": bc must be 0 or 1"); delete B; return nullptr; }
+    // periodic, transmissive or reflecting walls (isothermal walls run in the single-problem
+    // FP64 form only)
+    if (q.bc_x < 0 || q.bc_x > 2 || q.bc_y < 0 || q.bc_y > 2) { bfail(GKS_EINVAL, "problem " + std::to_string(p) + ": bc must be 0, 1 or 2"); delete B; return nullptr; }
     const int dim = q.ny > 1 ? 2 : 1, N = dim + 2;
-    if (dim == 2 && (q.recon == 1 || q.mu > 0.0)) B->cls = 1;
-    if (dim == 1 && q.mu > 0.0) B->cls = 1;
+    if (dim == 2 && (q.recon == 1 || q.mu > 0.0)) B->cls = std::max(B->cls, 1);
+    if (dim == 1 && q.mu > 0.0) B->cls = std::max(B->cls, 1);
+    if (q.bc_x == 2 || (dim == 2 && q.bc_y == 2)) B->cls = 2;   // the kernel with the wall signs
     const long nc = (long)q.nx * q.ny;
     B->ncell[p] = nc;
     const long L = N * nc;

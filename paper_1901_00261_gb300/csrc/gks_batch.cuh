@@ -31,11 +31,13 @@ struct BatchArgs {
 };
 
 // Item dispatch.  CLASS 0: 1D (linear / WENO-Z, Euler) and 2D linear Euler problems;
-// CLASS 1: every problem kind (2D WENO-Z, Navier-Stokes).
+// CLASS 1: every problem kind (2D WENO-Z, Navier-Stokes); CLASS 2: every problem kind, with
+// the sweeps compiled with the reflecting-wall signs (a batch holding a walled problem).
 template <int CLASS, int FPT>
 __device__ __forceinline__ void run_item(const BatchProblem& P, int phase, int kind, int tile, int tid,
                                          float* smf) {
   const int stage = phase < 2 ? 0 : 1;
+  constexpr bool WL = CLASS == 2;
   if (phase == 0 || phase == 2) {
     const FaceArgs32& a = kind == 0 ? P.ax[stage] : P.ay[stage];
     const bool visc = a.P.mu > 0.0;
@@ -46,14 +48,14 @@ __device__ __forceinline__ void run_item(const BatchProblem& P, int phase, int k
         const int f = base + r * (TA32 * TB32) + tid;
         // the MSMD stage (index 0 / 1) picks the stage-1 / stage-2 instantiation
 #define GKS_SWEEP1D(O, WN, VS) \
-  (stage == 0 ? sweep1d_f32_face_call<O, WN, VS, 1>(a, f) : sweep1d_f32_face_call<O, WN, VS, 2>(a, f))
+  (stage == 0 ? sweep1d_f32_face_call<O, WN, VS, 1, WL>(a, f) : sweep1d_f32_face_call<O, WN, VS, 2, WL>(a, f))
         if (P.order == 6) {
           if (P.recon == 0) GKS_SWEEP1D(6, false, false);
-          else if (CLASS == 1 && visc) GKS_SWEEP1D(6, true, true);
+          else if (CLASS != 0 && visc) GKS_SWEEP1D(6, true, true);
           else GKS_SWEEP1D(6, true, false);
         } else {
           if (P.recon == 0) GKS_SWEEP1D(8, false, false);
-          else if (CLASS == 1 && visc) GKS_SWEEP1D(8, true, true);
+          else if (CLASS != 0 && visc) GKS_SWEEP1D(8, true, true);
           else GKS_SWEEP1D(8, true, false);
         }
       }
@@ -62,9 +64,9 @@ __device__ __forceinline__ void run_item(const BatchProblem& P, int phase, int k
     }
     const int tbx = kind == 0 ? P.tbx_x : P.tbx_y;
     const int bx = tile % tbx, by = tile / tbx;
-#define GKS_SWEEP2D(O, WN, VS, D)                                          \
-  (stage == 0 ? sweep2d_f32_tile_call<O, WN, VS, D, FPT, 1>(a, bx, by, tid, smf) \
-              : sweep2d_f32_tile_call<O, WN, VS, D, FPT, 2>(a, bx, by, tid, smf))
+#define GKS_SWEEP2D(O, WN, VS, D)                                              \
+  (stage == 0 ? sweep2d_f32_tile_call<O, WN, VS, D, FPT, 1, WL>(a, bx, by, tid, smf) \
+              : sweep2d_f32_tile_call<O, WN, VS, D, FPT, 2, WL>(a, bx, by, tid, smf))
     if (CLASS == 0) {
       if (kind == 0) { if (P.order == 6) GKS_SWEEP2D(6, false, false, 0); else GKS_SWEEP2D(8, false, false, 0); }
       else { if (P.order == 6) GKS_SWEEP2D(6, false, false, 1); else GKS_SWEEP2D(8, false, false, 1); }
@@ -153,13 +155,16 @@ size_t batch_smem() {
 
 typedef void (*BatchKernelFn)(BatchArgs);
 
-// Instantiated in gks_batch_k<FPT>.cu: the persistent kernel of class `cls` and its dynamic
-// shared memory.
+// Instantiated in gks_batch_k<FPT>.cu (classes 0 and 1) and gks_batch_w<FPT>.cu (class 2):
+// the persistent kernel of class `cls` and its dynamic shared memory.
 BatchKernelFn batch_kernel_fpt1(int cls);
 BatchKernelFn batch_kernel_fpt2(int cls);
 BatchKernelFn batch_kernel_fpt4(int cls);
 size_t batch_smem_fpt1(int cls);
 size_t batch_smem_fpt2(int cls);
 size_t batch_smem_fpt4(int cls);
+BatchKernelFn batch_kernel_walls_fpt1();
+BatchKernelFn batch_kernel_walls_fpt2();
+BatchKernelFn batch_kernel_walls_fpt4();
 
 }  // namespace gks

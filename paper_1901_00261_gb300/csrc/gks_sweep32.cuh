@@ -730,13 +730,13 @@ __global__ void __launch_bounds__(256, 3) update_f32_kernel(UpdateArgs32 a) {
 // batch kernel's size and register allocation stay bounded instead of inlining every
 // variant.  The standalone kernels inline the same bodies; the compiler may contract
 // multiply-adds differently in the two, so the two agree to single-precision rounding.
-template <int ORDER, bool WENO, bool VISC, int STAGE>
+template <int ORDER, bool WENO, bool VISC, int STAGE, bool WALLS = false>
 __device__ __noinline__ void sweep1d_f32_face_call(const FaceArgs32& a, int f) {
-  sweep1d_f32_face<ORDER, WENO, VISC, true, STAGE>(a, f);
+  sweep1d_f32_face<ORDER, WENO, VISC, true, STAGE, WALLS>(a, f);
 }
-template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE>
+template <int ORDER, bool WENO, bool VISC, int DIR, int FPT, int STAGE, bool WALLS = false>
 __device__ __noinline__ void sweep2d_f32_tile_call(const FaceArgs32& a, int bx, int by, int tid, float* smf) {
-  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, true, FPT, STAGE>(a, bx, by, tid, smf);
+  sweep2d_f32_tile<ORDER, WENO, VISC, DIR, true, FPT, STAGE, WALLS>(a, bx, by, tid, smf);
 }
 template <int DIM, int STAGE>
 __device__ __noinline__ void update_f32_cell_call(const UpdateArgs32& a, long c) {

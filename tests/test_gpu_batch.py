@@ -243,3 +243,45 @@ def test_batch_members_match_the_oracle_per_step():
                     err = np.abs(a[v] - b[v]).max() / max(scale, 1e-300)
                     assert err <= (tw if a_i == 0 else ts), \
                         f"step {step} problem {k} ({kinds[k]}, {st.nx}x{st.ny}) array {a_i} var {v}: {err:.3e}"
+
+
+def test_batch_with_reflecting_walls():
+    """Walled problems (1D wall impact; 2D box pulses between walls on one or both axes,
+    linear and WENO-Z) in one batch with a periodic vortex: the batch then runs the persistent
+    kernel compiled with the wall signs.  Every member matches its standalone FP32-bulk run,
+    and a walled member's step matches the oracle's within the FP32-bulk bounds."""
+    states = [inputs.wall_impact_1d(300, order=8),
+              inputs.box_pulse_2d(40, ny=36),
+              inputs.box_pulse_2d(32, ny=28, order=6, recon=1),
+              inputs.box_pulse_2d(30, ny=35, recon=1, bc_x=1),
+              inputs.box_pulse_2d(33, ny=27, order=6, bc_y=0),
+              inputs.isentropic_vortex_2d(24, order=8, recon=0, ny=20)]
+    dts = dts_of(states)
+    for fpt in (1, 2, 4):
+        B = gks.Batch(states)
+        set_config_fitting(B, fpt, B.config()[1])
+        B.steps(dts, 3)
+        for k, st in enumerate(states):
+            assert_close_to_alone(B.get_state(k), run_alone(st, dts[k], 3), st,
+                                  f"fpt {fpt} problem {k} ({st.name}, {st.nx}x{st.ny})")
+    st = states[1]
+    B = gks.Batch(states)
+    before = B.get_state(1)
+    B.steps(dts, 1)
+    ref = _oracle_step(st, *before, dts[1])
+    got = B.get_state(1)
+    tw, ts = ORACLE_BOUNDS["linear"]
+    for a_i, (a, b) in enumerate(zip(got, ref)):
+        for v in range(b.shape[0]):
+            scale = np.abs(b[v]).max()
+            if a_i > 0:
+                scale = max(scale, np.abs(ref[0][v]).max() / (st.dx if a_i == 1 else st.dy))
+            err = np.abs(a[v] - b[v]).max() / max(scale, 1e-300)
+            assert err <= (tw if a_i == 0 else ts), f"array {a_i} var {v}: {err:.3e}"
+
+
+def test_batch_rejects_isothermal_walls():
+    st = inputs.box_pulse_2d(16, ny=16)
+    st.bc_x = 3
+    with pytest.raises(gks.GksError):
+        gks.Batch([st])
