@@ -73,13 +73,17 @@ KERNEL_MODEL = {
     ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
                                                 "traffic": 373.2, "winstr": 703},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
-    # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face from a 1024^2 capture
-    ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 11501.0, "f64": 427.0},
-    ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10185.0, "f64": 427.0},
-    ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 11389.0, "f64": 396.0},
-    ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 10073.0, "f64": 396.0},
-    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0},
-    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0},
+    # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face and warp-instructions per
+    # 32 faces from one-pass instruction-counter captures of the 4096^2 step (the FP64 count
+    # depends on the grid through dt/tau: the time coefficients' series length follows it)
+    ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 11479.5, "f64": 243.6, "winstr": 10584},
+    ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10170.4, "f64": 243.5, "winstr": 9366},
+    ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 10915.5, "f64": 146.6, "winstr": 9555},
+    ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 9606.4, "f64": 146.5, "winstr": 8381},
+    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
+                                            "traffic": 285.5},
+    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
+                                            "traffic": 381.5},
 }
 HBM_FALLBACK_GBS = 6800.0
 
