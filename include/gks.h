@@ -132,6 +132,16 @@ int gks_get_state(gks_ctx* ctx, double* W, double* Wx, double* Wy);
 int gks_set_state_device(gks_ctx* ctx, const double* W, const double* Wx, const double* Wy);
 int gks_get_state_device(gks_ctx* ctx, double* W, double* Wx, double* Wy);
 
+/* Rows [j0, j0 + nrows) of the 2D state (W, Wx, Wy, each [nvar][ny][nx]) to or from a packed
+ * caller-owned device buffer buf laid out [3][nvar][nrows][nx] (W rows, then Wx, then Wy),
+ * ordered on the context stream, asynchronous (no host synchronisation): the halo exchange of
+ * a row-split decomposition (one problem spread over several GPUs, each holding a slab of
+ * rows plus halo rows that its neighbours' steps refresh).  set_rows also refreshes the
+ * FP32-bulk form's float mirror of those rows.  GKS_EINVAL for a NULL argument, a 1D context,
+ * or rows outside [0, ny). */
+int gks_get_rows_device(gks_ctx* ctx, int j0, int nrows, double* buf);
+int gks_set_rows_device(gks_ctx* ctx, int j0, int nrows, const double* buf);
+
 /* Advance one two-stage MSMD step of size dt > 0 (asynchronous on the context stream). */
 int gks_step(gks_ctx* ctx, double dt);
 
@@ -200,6 +210,12 @@ int gks_probe_time_coefs_single(const double* theta, int n, double dt, double* o
  * single-precision reciprocal refined by two Newton-Raphson steps in FP64.  Synchronous;
  * GKS_EINVAL for a NULL array or n < 0. */
 int gks_probe_rcp64(const double* x, int n, double* out);
+
+/* Test probe of the double -> float conversion the FP32-bulk form uses for the float mirror of
+ * the slopes (not part of the method): out[i] (host float array) = x[i] (host, n >= 0 entries,
+ * any value) rounded to the nearest float, ties to even, as the device forms it on its integer
+ * pipes.  Synchronous; GKS_EINVAL for a NULL array or n < 0. */
+int gks_probe_d2f(const double* x, int n, float* out);
 
 /* Release everything the context owns.  NULL is ignored. */
 void gks_destroy(gks_ctx* ctx);

@@ -325,6 +325,39 @@ int gks_set_state_device(gks_ctx* c, const double* W, const double* Wx, const do
   return refresh_mirror(c);
 }
 
+namespace {
+// One 2D copy of rows [j0, j0 + nrows) of every state plane (W, Wx, Wy; nvar planes each)
+// between the state and a packed buffer [dim + 1][nvar][nrows][nx].
+int copy_rows(gks_ctx* c, int j0, int nrows, double* buf, bool to_state, const char* what) {
+  if (!c || !buf) return fail(GKS_EINVAL, "NULL argument%s");
+  if (c->dim != 2) return fail(GKS_EINVAL, "rows exist in 2D only%s");
+  if (j0 < 0 || nrows < 1 || (long)j0 + nrows > c->ny) return fail(GKS_EINVAL, "rows outside the grid%s");
+  if (int jrc = join_pipeline(c)) return jrc;
+  const size_t plane = (size_t)c->ny * c->nx * sizeof(double);
+  const size_t width = (size_t)nrows * c->nx * sizeof(double);
+  const size_t nplanes = (size_t)(c->dim + 1) * c->nv;
+  double* rows = c->state + (size_t)j0 * c->nx;
+  cudaError_t e = to_state
+      ? cudaMemcpy2DAsync(rows, plane, buf, width, width, nplanes, cudaMemcpyDeviceToDevice, c->stream)
+      : cudaMemcpy2DAsync(buf, width, rows, plane, width, nplanes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (!to_state || c->o.precision != GKS_PREC_FP32_BULK) return GKS_OK;
+  // the float mirror of the replaced rows (all of it if it holds a pipeline slot's state)
+  if (c->mirror_foreign) return refresh_mirror(c);
+  e = gks::launch_mirror_rows(c->state, c->mirror, c->nx, c->ny, c->dim, j0, nrows, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mirror");
+  return GKS_OK;
+}
+}  // namespace
+
+int gks_get_rows_device(gks_ctx* c, int j0, int nrows, double* buf) {
+  return copy_rows(c, j0, nrows, buf, false, "get_rows_device copy");
+}
+
+int gks_set_rows_device(gks_ctx* c, int j0, int nrows, const double* buf) {
+  return copy_rows(c, j0, nrows, const_cast<double*>(buf), true, "set_rows_device copy");
+}
+
 int gks_get_state(gks_ctx* c, double* W, double* Wx, double* Wy) {
   if (!c || !W || !Wx || (c->dim == 2 && !Wy)) return fail(GKS_EINVAL, "NULL argument%s");
   if (int jrc = join_pipeline(c)) return jrc;
@@ -443,6 +476,14 @@ int gks_probe_time_coefs(const double* theta, int n, double dt, double* out) {
 
 int gks_probe_time_coefs_single(const double* theta, int n, double dt, double* out) {
   return probe_time_coefs_checked(theta, n, dt, out, true);
+}
+
+int gks_probe_d2f(const double* x, int n, float* out) {
+  if (!x || !out || n < 0) return fail(GKS_EINVAL, "NULL argument or n < 0%s");
+  if (n == 0) return GKS_OK;
+  cudaError_t e = gks::probe_d2f(x, n, out);
+  if (e != cudaSuccess) return cuda_fail(e, "conversion probe");
+  return GKS_OK;
 }
 
 int gks_probe_rcp64(const double* x, int n, double* out) {

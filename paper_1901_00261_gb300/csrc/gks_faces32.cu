@@ -4,10 +4,16 @@
 namespace gks {
 
 cudaError_t launch_mirror(const double* S, float* M, int nx, int ny, int dim, cudaStream_t s) {
-  long ncell = (long)nx * ny;
-  unsigned blocks = (unsigned)((ncell + 255) / 256);
-  if (dim == 1) mirror_kernel<1><<<blocks, 256, 0, s>>>(S, M, ncell);
-  else mirror_kernel<2><<<blocks, 256, 0, s>>>(S, M, ncell);
+  return launch_mirror_rows(S, M, nx, ny, dim, 0, ny, s);
+}
+
+cudaError_t launch_mirror_rows(const double* S, float* M, int nx, int ny, int dim, int j0, int nrows,
+                               cudaStream_t s) {
+  const long ncell = (long)nx * ny, c0 = (long)j0 * nx, n = (long)nrows * nx;
+  if (n <= 0) return cudaSuccess;
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (dim == 1) mirror_kernel<1><<<blocks, 256, 0, s>>>(S, M, ncell, c0, n);
+  else mirror_kernel<2><<<blocks, 256, 0, s>>>(S, M, ncell, c0, n);
   return cudaGetLastError();
 }
 
@@ -47,6 +53,28 @@ cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon
 __global__ void rcp64_probe_kernel(const double* x, int n, double* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = rcp64(x[i]);
+}
+
+__global__ void d2f_probe_kernel(const double* x, int n, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = d2f_int(x[i]);
+}
+
+// d2f_int of host x[0..n) into host out[0..n); synchronous (test probe).
+cudaError_t probe_d2f(const double* x, int n, float* out) {
+  double* d = nullptr;
+  float* o = nullptr;
+  cudaError_t e = cudaMalloc(&d, (size_t)n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&o, (size_t)n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    d2f_probe_kernel<<<(n + 127) / 128, 128>>>(d, n, o);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, o, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (o) cudaFree(o);
+  return e;
 }
 
 // rcp64 of host x[0..n) into host out[0..n); synchronous (test probe).

@@ -8,14 +8,25 @@
 
 namespace gks {
 
-// Face rows per thread of the standalone 2D sweep tiles (TA32 x TB32 * SWEEP32_FPT faces).
+// Face rows per thread of the standalone 2D sweep tiles (TA32 x TB32 * FPT faces): linear
+// Euler tiles SWEEP32_FPT; WENO-Z / viscous tiles SWEEP32_FPT_NX (x faces) and
+// SWEEP32_FPT_NY (y faces).  The WENO-Z / viscous tiles run two blocks per SM, bound by
+// registers, whatever their height, so their taller tiles cost no occupancy and an x-face
+// tile reconstructs 1.25 slots per face instead of 1.5 (4096^2 shear layer, ms per step:
+// 38.6 with 4 / 4 rows, 39.3 with 4 / 2, 40.0 with 2 / 2, 42.2 with 1 / 2).
 #ifndef SWEEP32_FPT
 #define SWEEP32_FPT 2
+#endif
+#ifndef SWEEP32_FPT_NX
+#define SWEEP32_FPT_NX 4
+#endif
+#ifndef SWEEP32_FPT_NY
+#define SWEEP32_FPT_NY 4
 #endif
 
 template <int ORDER, bool WENO, bool VISC, int DIR, bool WALLS, bool TANW>
 inline cudaError_t launch_2d32_t(const FaceArgs32& a, cudaStream_t s) {
-  const int FPT = SWEEP32_FPT;
+  constexpr int FPT = !(WENO || VISC) ? SWEEP32_FPT : (DIR == 0 ? SWEEP32_FPT_NX : SWEEP32_FPT_NY);
   typedef Tile32<DIR, FPT> T;
   const size_t shmem = T::smem_bytes(WENO);
   static std::atomic<unsigned long long> smem_set{0};

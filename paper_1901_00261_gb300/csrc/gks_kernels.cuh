@@ -105,6 +105,9 @@ struct UpdateArgs32 {
 
 // launchers (defined in the .cu units)
 cudaError_t launch_mirror(const double* S, float* M, int nx, int ny, int dim, cudaStream_t s);
+// the mirror of rows [j0, j0 + nrows) only
+cudaError_t launch_mirror_rows(const double* S, float* M, int nx, int ny, int dim, int j0, int nrows,
+                               cudaStream_t s);
 cudaError_t launch_faces32_1d(const FaceArgs32& a, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_faces32_2d(const FaceArgs32& a, int dir, int order, int recon, bool visc, cudaStream_t s);
 cudaError_t launch_update32(const UpdateArgs32& a, int dim, int stage, cudaStream_t s);
@@ -120,5 +123,6 @@ cudaError_t probe_time_coefs(const double* theta, int n, double dt, double* out,
 
 // Test probe: the FP32-bulk sweeps' FP64 reciprocal of host x[0..n) into host out.
 cudaError_t probe_rcp64(const double* x, int n, double* out);
+cudaError_t probe_d2f(const double* x, int n, float* out);
 
 }  // namespace gks

@@ -34,6 +34,22 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// double -> float rounded to nearest (ties to even) on the integer pipes: for results in the
+// normal float range the sign, the rebiased exponent (1023 -> 127) and the top 23 fraction
+// bits are moved into place and the 29 dropped bits decide the rounding (a carry out of the
+// fraction steps the exponent, up to inf); zero, subnormal results, inf and nan take the
+// conversion instruction.  Bitwise equal to __double2float_rn (tested through gks_probe_d2f).
+__device__ __forceinline__ float d2f_int(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(d);
+  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  return __uint_as_float(f);
+}
+
 // 1/x for a positive normal x within the float range: a single-precision seed refined by
 // two Newton-Raphson steps for f(r) = 1/r - x, r <- r + r (1 - x r), in FP64 (each squares
 // the relative error, from ~2^-23 to below FP64 rounding: within a few ulp of 1/x, tested
@@ -130,8 +146,7 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
 //   FP64 dW  = W_right - W_left of the face's two cells    (stage 1)
 //   FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt     (stage 1)
 //   FP32 dLT = W0 - W_ref + dt W_t + dt^2/6 W_tt          (stage 1; stage 2 adds dt^2/3 W_tt*)
-//   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1; the stage-1 update then
-//        replaces D by the single-precision cell difference float(dW))
+//   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1; read by the stage-1 update)
 // F_ref = F_Euler(W_left) in FP64 (W_ref = W_left is the face's reference state), dF and F_t the
 // single-precision flux delta and derivative, dFc = F_Euler(W_right) - F_Euler(W_left) in the
 // single-precision delta form.  Xi is one FP64 value per face, so its differences across a
@@ -582,11 +597,11 @@ faces_2d_f32_kernel(FaceArgs32 a) {
 //     of W^n plus the single-precision increment -(A_{i+1/2} + D_{i-1/2})/dx - (..)/dy, added
 //     exactly (two-sum) and renormalised; the W* slopes (dW + dOmega_{i+1/2} - dOmega_{i-1/2})/dx
 //     as floats.
-//   Stage 2 (float mirror of the slopes: (float(dW) + dLT_{i+1/2} - dLT_{i-1/2})/dx, single
-//     precision, float(dW) left in the D plane by stage 1):
-//     W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
+//   Stage 2: W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
 //     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
-//     place (each cell reads only its own state), and the mirror of W^{n+1}.
+//     place (each cell reads only its own state), and the mirror of W^{n+1} exactly as
+//     write_mirror builds it from the FP64 state (hi/lo of W, the slopes rounded to float), so
+//     a run restarted from its FP64 state continues bit for bit.
 // ---------------------------------------------------------------------------
 // FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
 template <int DIM>
@@ -600,16 +615,18 @@ __device__ __forceinline__ void write_mirror(float* M, long c, long ncell, const
     split_hilo(w[v], hi, lo);
     M[v * ncell + c] = hi;
     M[L + v * ncell + c] = lo;
-    M[2 * L + v * ncell + c] = (float)wx[v];
-    if (DIM == 2) M[3 * L + v * ncell + c] = (float)wy[v];
+    M[2 * L + v * ncell + c] = d2f_int(wx[v]);
+    if (DIM == 2) M[3 * L + v * ncell + c] = d2f_int(wy[v]);
   }
 }
 
+// Cells [c0, c0 + n) of a state of ncell cells.
 template <int DIM>
-__global__ void __launch_bounds__(256) mirror_kernel(const double* S, float* M, long ncell) {
+__global__ void __launch_bounds__(256) mirror_kernel(const double* S, float* M, long ncell, long c0, long n) {
   const int N = DIM + 2;
-  long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long c = c0 + i;
   const long L = N * ncell;
   double w[N], wx[N], wy[N];
 #pragma unroll
@@ -638,7 +655,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   const float idxf = (float)idx, idyf = (float)idy;
   float* M = a.M;
   if (STAGE == 1) {
-    // all loads first (the D-plane stores below could otherwise alias them and serialise)
+    // all loads first
     float h0[N], lo0[N], Ax[N], Dxv[N], Ol[N], Or[N], dWx[N];
     float Ay[N], Dyv[N], Ob[N], Ot[N], dWy[N];
 #pragma unroll
@@ -667,10 +684,6 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
         inc += (Ay[v] + Dyv[v]) * idyf;
         wys = (dWy[v] + (Ot[v] - Ob[v])) * idyf;
       }
-      // D at this cell's left (bottom) face is read only by this cell: it is replaced by the
-      // FP32 cell difference dW, which the stage-2 update uses for the float mirror of the slopes
-      x32[(3L * N + v) * nfx + fxl] = dWx[v];
-      if (DIM == 2) y32[(3L * N + v) * nfy + fyb] = dWy[v];
       // W* = W + d as hi/lo: exact two-sum of the cell's hi with d, renormalised
       const float d = -inc;
       const float s1 = h0[v] + d;
@@ -685,7 +698,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   } else {
     // all loads first, then the FP64 accumulation and the stores
     double W0[N], Xl[N], Xr[N], dWx[N], Yb[N], Yt[N], dWy[N];
-    float dLx[N], fWx[N], dLy[N], fWy[N];
+    float dLx[N], dLy[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       W0[v] = ldd<CG>(a.W + v * ncell + c);
@@ -693,24 +706,26 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       Xr[v] = ldd<CG>(x64 + (long)v * nfx + fxl + 1);
       dWx[v] = ldd<CG>(x64 + (long)(N + v) * nfx + fxl);
       dLx[v] = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
-      fWx[v] = ldf<CG>(x32 + (3L * N + v) * nfx + fxl);
       if (DIM == 2) {
         Yb[v] = ldd<CG>(y64 + (long)v * nfy + fyb);
         Yt[v] = ldd<CG>(y64 + (long)v * nfy + fyt);
         dWy[v] = ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
         dLy[v] = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
-        fWy[v] = ldf<CG>(y32 + (3L * N + v) * nfy + fyb);
       }
     }
 #pragma unroll
     for (int v = 0; v < N; ++v) {
+      // the slopes (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2}) / dx in FP64, and their float
+      // mirror as the FP64 slope rounded (the mirror write_mirror would build from the state)
       double w = W0[v] - (Xr[v] - Xl[v]) * idx;
-      a.W[L + v * ncell + c] = fma(dWx[v], idx, f2d_int(dLx[v] * idxf));
-      M[2 * L + v * ncell + c] = (fWx[v] + dLx[v]) * idxf;   // (dW + dLT_{i+1/2} - dLT_{i-1/2}) / dx
+      const double sx = fma(dWx[v], idx, f2d_int(dLx[v] * idxf));
+      a.W[L + v * ncell + c] = sx;
+      M[2 * L + v * ncell + c] = d2f_int(sx);
       if (DIM == 2) {
         w -= (Yt[v] - Yb[v]) * idy;
-        a.W[2 * L + v * ncell + c] = fma(dWy[v], idy, f2d_int(dLy[v] * idyf));
-        M[3 * L + v * ncell + c] = (fWy[v] + dLy[v]) * idyf;
+        const double sy = fma(dWy[v], idy, f2d_int(dLy[v] * idyf));
+        a.W[2 * L + v * ncell + c] = sy;
+        M[3 * L + v * ncell + c] = d2f_int(sy);
       }
       a.W[v * ncell + c] = w;
       float hi, lo;

@@ -14,9 +14,12 @@ transmissive boundary on its halo rows, whose effect never reaches the slab's ow
 one step.  Periodic y: the slabs form a ring.
 
 The exchange runs through torch.distributed (gloo on the CPU, NCCL between GPUs) as one
-all_gather of every rank's two boundary blocks.  The solver of a slab is any object with
+all_gather of every rank's two boundary blocks.  DecomposedRun takes any solver with
 set_state(W, Wx, Wy), step(dt) and get_state() on host arrays [nvar][rows][nx] (the library's
-gks.Solver, or, in the tests, the CPU reference), built by a caller-supplied factory.
+gks.Solver, or, in the tests, the CPU reference) and moves the slab through host memory each
+step; DeviceDecomposedRun keeps the slab resident on its GPU (a gks.Solver) and moves only
+the boundary and halo rows, device to device (gks_get_rows_device / gks_set_rows_device and
+a device all_gather).  Both build the slab's solver with a caller-supplied factory.
 """
 from __future__ import annotations
 
@@ -157,17 +160,93 @@ class DecomposedRun:
     def gather(self):
         """The global state assembled on every rank (all_gather of the slabs, each padded to
         the largest slab's rows)."""
-        own = self.own_state()
-        if self.slab.nranks == 1:
-            return own
+        return gather_slabs(self.slab, self.own_state(), self.dist)
+
+
+def gather_slabs(slab: Slab, own, dist):
+    """Assemble the global arrays from every rank's own rows (host arrays [nvar][rows][nx])."""
+    if slab.nranks == 1:
+        return own
+    import torch
+    sizes = [j1 - j0 for j0, j1 in slab.ranges]
+    m = max(sizes)
+    out = []
+    for a in own:
+        pad = torch.zeros((a.shape[0], m, a.shape[2]), dtype=torch.float64)
+        pad[:, :a.shape[1], :] = torch.from_numpy(a)
+        got = [torch.empty_like(pad) for _ in sizes]
+        dist.all_gather(got, pad)
+        out.append(torch.cat([g[:, :n, :] for g, n in zip(got, sizes)], dim=1).numpy())
+    return out
+
+
+class DeviceDecomposedRun:
+    """One 2D problem advanced by `nranks` ranks with every slab resident on its GPU.
+
+    make_solver(ny_ext, y0, y1, bc_y) builds the slab's gks.Solver (same nx, x domain,
+    physics, scheme and precision as the global problem).  Per step: the slab's step; its
+    first and last `halo` own rows of W, Wx, Wy packed on the device (gks_get_rows_device);
+    one all_gather of the packed blocks (NCCL: device to device; another backend: staged
+    through host memory); the neighbours' blocks written into the halo rows
+    (gks_set_rows_device, which also refreshes the FP32-bulk form's float mirror of them).
+    2 halo x 3 arrays x nvar x nx doubles per rank and step travel, nothing else."""
+
+    def __init__(self, W, Wx, Wy, y0: float, y1: float, bc_y: int, make_solver, rank: int,
+                 nranks: int, dist=None, halo: int = HALO, device=None):
         import torch
-        sizes = [j1 - j0 for j0, j1 in self.slab.ranges]
-        m = max(sizes)
-        out = []
-        for a in own:
-            pad = torch.zeros((self.nvar, m, self.nx), dtype=torch.float64)
-            pad[:, :a.shape[1], :] = torch.from_numpy(a)
-            got = [torch.empty_like(pad) for _ in sizes]
-            self.dist.all_gather(got, pad)
-            out.append(torch.cat([g[:, :n, :] for g, n in zip(got, sizes)], dim=1).numpy())
-        return out
+        self.nvar, ny, self.nx = W.shape
+        self.slab = Slab(ny, rank, nranks, bc_y == 0, halo)
+        self.dist = dist
+        ly0, ly1 = self.slab.local_y_range(y0, y1)
+        self.solver = make_solver(self.slab.n_ext, ly0, ly1, self.slab.local_bc_y(bc_y))
+        self.solver.set_state(*[self.slab.extract(A) for A in (W, Wx, Wy)])
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.mine = torch.empty((2, 3, self.nvar, halo, self.nx), dtype=torch.float64,
+                                device=self.device)
+        self._staged = dist is not None and dist.get_backend() != "nccl"
+
+    def pack(self):
+        """This rank's boundary blocks [2][3][nvar][halo][nx] (device; synchronised)."""
+        o, h = self.slab.own, self.slab.halo
+        self.solver.get_rows_device(o.start, h, self.mine[0].data_ptr())
+        self.solver.get_rows_device(o.stop - h, h, self.mine[1].data_ptr())
+        self.solver.sync()
+        return self.mine
+
+    def unpack(self, parts):
+        """Write the neighbours' boundary blocks (parts[r] = rank r's pack()) into the halo
+        rows."""
+        import torch
+        h = self.slab.halo
+        torch.cuda.current_stream(self.device).synchronize()
+        if self.slab.lower is not None:
+            blk = parts[self.slab.lower][1].to(self.device).contiguous()
+            self.solver.set_rows_device(0, h, blk.data_ptr())
+            self._keep = blk
+        if self.slab.upper is not None:
+            blk2 = parts[self.slab.upper][0].to(self.device).contiguous()
+            self.solver.set_rows_device(self.slab.n_ext - h, h, blk2.data_ptr())
+            self._keep2 = blk2
+        self.solver.sync()
+
+    def step(self, dt: float) -> None:
+        """One two-stage step of the whole problem: the slab's step, then the halo exchange."""
+        self.solver.step(dt)
+        if self.slab.nranks == 1:
+            return
+        import torch
+        mine = self.pack()
+        if self._staged:
+            mine = mine.cpu()
+        parts = [torch.empty_like(mine) for _ in range(self.slab.nranks)]
+        self.dist.all_gather(parts, mine)
+        self.unpack(parts)
+
+    def own_state(self):
+        """This slab's own rows of W, Wx, Wy (host arrays)."""
+        W, Wx, Wy = self.solver.get_state()
+        o = self.slab.own
+        return [a[:, o, :].copy() for a in (W, Wx, Wy)]
+
+    def gather(self):
+        return gather_slabs(self.slab, self.own_state(), self.dist)

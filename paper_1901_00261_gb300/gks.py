@@ -55,6 +55,8 @@ SIGNATURES = {
     "gks_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gks_set_state_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gks_get_state_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_get_rows_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "gks_set_rows_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "gks_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "gks_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     "gks_max_wavespeed": (ctypes.c_int, [ctypes.c_void_p, _DP]),
@@ -68,6 +70,7 @@ SIGNATURES = {
     "gks_probe_time_coefs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
     "gks_probe_time_coefs_single": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _DP]),
     "gks_probe_rcp64": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
+    "gks_probe_d2f": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_void_p]),
     "gks_step_1d_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -227,6 +230,14 @@ class Solver:
         _check(lib().gks_get_state_device(self._h, ctypes.c_void_p(W_ptr), ctypes.c_void_p(Wx_ptr),
                                           ctypes.c_void_p(Wy_ptr) if Wy_ptr else None))
 
+    def get_rows_device(self, j0: int, nrows: int, buf_ptr: int):
+        """Rows [j0, j0 + nrows) of W, Wx, Wy into the device buffer [3][nvar][nrows][nx]."""
+        _check(lib().gks_get_rows_device(self._h, int(j0), int(nrows), ctypes.c_void_p(buf_ptr)))
+
+    def set_rows_device(self, j0: int, nrows: int, buf_ptr: int):
+        """Rows [j0, j0 + nrows) of W, Wx, Wy from the device buffer [3][nvar][nrows][nx]."""
+        _check(lib().gks_set_rows_device(self._h, int(j0), int(nrows), ctypes.c_void_p(buf_ptr)))
+
     def step(self, dt: float):
         _check(lib().gks_step(self._h, float(dt)))
 
@@ -293,6 +304,14 @@ def probe_rcp64(x) -> np.ndarray:
     xx = np.ascontiguousarray(x, dtype=np.float64).ravel()
     out = np.zeros(xx.size)
     _check(lib().gks_probe_rcp64(xx.ctypes.data_as(_DP), xx.size, out.ctypes.data_as(_DP)))
+    return out
+
+
+def probe_d2f(x) -> np.ndarray:
+    """The FP32-bulk form's double -> float rounding of each x, evaluated on the device."""
+    xx = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.zeros(xx.size, dtype=np.float32)
+    _check(lib().gks_probe_d2f(xx.ctypes.data_as(_DP), xx.size, ctypes.c_void_p(out.ctypes.data)))
     return out
 
 

@@ -92,6 +92,9 @@ def test_null_context_calls_fail_cleanly():
     assert L.gks_step_host_async(None, None, None, None, None, None, None, 0.1) == gks.GKS_EINVAL
     assert L.gks_probe_time_coefs(None, 1, 0.1, None) == gks.GKS_EINVAL
     assert L.gks_probe_time_coefs_single(None, 1, 0.1, None) == gks.GKS_EINVAL
+    assert L.gks_get_rows_device(None, 0, 1, None) == gks.GKS_EINVAL
+    assert L.gks_probe_d2f(None, 1, None) == gks.GKS_EINVAL
+    assert L.gks_set_rows_device(None, 0, 1, None) == gks.GKS_EINVAL
     assert L.gks_get_state(None, None, None, None) == gks.GKS_EINVAL
     L.gks_destroy(None)
 
@@ -110,7 +113,7 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     (dict(recon=2), "recon"),
     (dict(gamma=1.0), "physics or domain"),
     (dict(x1=0.0), "physics or domain"),
-    (dict(bc_x=2), "bc"),
+    (dict(bc_x=3), "bc"),
 ])
 def test_batch_create_rejects_invalid_problems(mutate, msg):
     """Problem validation happens before any device work, so it is checked here without a GPU;

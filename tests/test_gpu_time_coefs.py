@@ -106,3 +106,27 @@ def test_rcp64_within_two_ulp_of_the_reciprocal():
 def test_rcp64_probe_rejects_null():
     L = gks.lib()
     assert L.gks_probe_rcp64(None, 1, None) == gks.GKS_EINVAL
+
+
+def test_d2f_rounds_to_nearest_even():
+    """The integer-pipe double -> float rounding of the FP32-bulk slope mirror equals IEEE
+    round-to-nearest-even (numpy's float32 conversion) bit for bit: random values across the
+    float range, exact ties between neighbouring floats (both parities), values next to the
+    largest float and rounding to infinity, subnormal results, signed zeros, inf and nan."""
+    rng = np.random.default_rng(17)
+    mant = rng.uniform(1.0, 2.0, 20000)
+    expo = rng.integers(-140, 128, 20000)
+    x = mant * np.exp2(expo.astype(float)) * np.where(rng.random(20000) < 0.5, -1.0, 1.0)
+    f = rng.uniform(1.0, 2.0, 4000).astype(np.float32) * np.float32(2.0) ** rng.integers(-120, 120, 4000).astype(np.float32)
+    nxt = np.nextafter(f, np.float32(np.inf))
+    ties = (f.astype(np.float64) + nxt.astype(np.float64)) / 2.0
+    fmax = float(np.finfo(np.float32).max)
+    edge = [fmax, fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24), 2.0 ** 128, 2.0 ** -126,
+            2.0 ** -126 * (1 - 2.0 ** -30), 2.0 ** -149, 2.0 ** -150, 1e-300, 0.0, -0.0,
+            np.inf, -np.inf, 1.0, -1.0, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 0.1, 1.0 / 3.0]
+    xs = np.concatenate([x, ties, -ties, np.array(edge)])
+    got = gks.probe_d2f(xs)
+    want = xs.astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    nan = gks.probe_d2f(np.array([np.nan]))
+    assert np.isnan(nan[0])
