@@ -64,14 +64,14 @@ KERNEL_MODEL = {
                                                  "winstr": 2303},
     ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 195.2,
                                                  "winstr": 2087},
-    ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
-                                                "traffic": 277.8, "winstr": 408},
+    ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0,
+                                                "traffic": 249.0, "winstr": 400},
     ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1826.6, "f64": 4.0, "traffic": 136.5,
                                                  "winstr": 1848},
     ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1750.0, "f64": 4.0, "traffic": 135.7,
                                                  "winstr": 1651},
-    ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
-                                                "traffic": 373.2, "winstr": 703},
+    ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0,
+                                                "traffic": 340.4, "winstr": 798},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face and warp-instructions per
     # 32 faces from one-pass instruction-counter captures of the 4096^2 step (the FP64 count
@@ -80,10 +80,8 @@ KERNEL_MODEL = {
     ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10170.4, "f64": 243.5, "winstr": 9366},
     ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 10915.5, "f64": 146.6, "winstr": 9555},
     ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 9606.4, "f64": 146.5, "winstr": 8381},
-    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 288.0,
-                                            "traffic": 285.5},
-    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 52.0, "f64": 40.0, "bytes": 384.0,
-                                            "traffic": 381.5},
+    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0},
+    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0},
 }
 HBM_FALLBACK_GBS = 6800.0
 
