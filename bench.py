@@ -633,11 +633,16 @@ def main():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        tw = time.perf_counter()
-        for k in range(e_steps):
-            G.step_host_async(ins, outs[k % 3], dt)
-        G.sync()
-        el = time.perf_counter() - tw
+        # three runs of e_steps calls; the median run is the value (the runtime places the two
+        # copy directions on the copy engines per run, and in some runs they do not overlap)
+        runs = []
+        for _ in range(3):
+            tw = time.perf_counter()
+            for k in range(e_steps):
+                G.step_host_async(ins, outs[k % 3], dt)
+            G.sync()
+            runs.append(time.perf_counter() - tw)
+        el = statistics.median(runs)
         L = gks.lib()
         ptr = lambda a: a.ctypes.data_as(gks.ctypes.c_void_p)  # noqa: E731
         o = outs[0]
@@ -653,7 +658,8 @@ def main():
         bytes_state = 3 * st.W.nbytes
         e2e = {"value": ncell * e_steps * ws / el, "unit": UNIT, "steps": e_steps,
                "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
-               "api": "gks_step_host_async (pipelined), then gks_sync",
+               "api": "gks_step_host_async (pipelined), then gks_sync; median of 3 runs",
+               "runs": [ncell * e_steps * ws / r for r in runs],
                "serial": {"value": ncell * e_steps * ws / el_serial,
                           "api": "gks_set_state + gks_step + gks_get_state per step"},
                "copy_gbs": pinned_copy_gbs(st.W.size * 3)}
