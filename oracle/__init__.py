@@ -70,8 +70,8 @@ def lib():
                                          c_double, dp, c_int, c_int, c_int, dp]
             L.orc_time_integrals.argtypes = [c_double, c_double, dp, dp]
             L.orc_eigvecs.argtypes = [c_int, c_double, dp, dp]
-            L.orc_point.argtypes = [c_int, c_double, c_double, c_double, c_int, c_int, dp,
-                                    c_double, dp]
+            L.orc_point.argtypes = [c_int, c_double, c_double, c_double, c_int, c_int, c_int,
+                                    dp, c_double, dp]
             L.orc_point.restype = c_int
             L.orc_create.argtypes = [c_int, c_int, c_double, c_double, c_double, c_int, c_int,
                                      c_int, c_int, c_double, c_double, c_double, c_double,
@@ -81,6 +81,8 @@ def lib():
             L.orc_set_eq_mode.argtypes = [c_void, c_int]
             L.orc_set_char_mode.argtypes = [c_void, c_int]
             L.orc_set_tan_mode.argtypes = [c_void, c_int]
+            L.orc_set_coef_mode.argtypes = [c_void, c_int]
+            L.orc_set_coef_mode.restype = c_int
             L.orc_set_walls.argtypes = [c_void, dp, dp]
             L.orc_set_walls.restype = c_int
             L.orc_iso_ghost.argtypes = [c_void, c_int, c_int, c_int, dp, dp]
@@ -207,7 +209,7 @@ POINT_FIELDS = ("W0", "W0x", "W0y", "W0xx", "W0xy", "W0yy", "Wl", "Wlx", "Wly", 
 
 
 def point(dim: int, gamma: float, mu: float, Pr: float, fields: dict, dt: float,
-          tau_mode: int = 0, flux_mode: int = 0) -> dict:
+          tau_mode: int = 0, flux_mode: int = 0, coef_mode: int = 0) -> dict:
     # (the equilibrium value is always the collision of Wl and Wr here; pass Wl = Wr = W0
     # for the linear scheme)
     """Gas-kinetic evaluation at one interface point (Eq. 3rd-simplify-flux)."""
@@ -217,7 +219,7 @@ def point(dim: int, gamma: float, mu: float, Pr: float, fields: dict, dt: float,
             v = np.asarray(fields[name], dtype=np.float64)
             pin[i, : v.size] = v
     out = np.zeros((5, 4))
-    rc = lib().orc_point(dim, gamma, mu, Pr, tau_mode, flux_mode, _p(pin), dt, _p(out))
+    rc = lib().orc_point(dim, gamma, mu, Pr, tau_mode, flux_mode, coef_mode, _p(pin), dt, _p(out))
     if rc != 0:
         raise ValueError("non-physical state")
     n = dim + 2
@@ -236,7 +238,7 @@ class Solver:
                  x0: float = 0.0, x1: float = 1.0, y0: float = 0.0, y1: float = 1.0,
                  weno_eps: float = 1e-6, tau_mode: int = 0, flux_mode: int = 0,
                  eq_mode: int = 1, char_mode: int = 0, tan_mode: int = 0,
-                 wall_T=(1.0, 1.0, 1.0, 1.0), wall_u=(0.0, 0.0, 0.0, 0.0)):
+                 wall_T=(1.0, 1.0, 1.0, 1.0), wall_u=(0.0, 0.0, 0.0, 0.0), coef_mode: int = 0):
         self.nx, self.ny = nx, ny
         self.dim = 2 if ny > 1 else 1
         self.nv = self.dim + 2
@@ -247,6 +249,10 @@ class Solver:
         lib().orc_set_eq_mode(self._h, int(eq_mode))
         lib().orc_set_char_mode(self._h, int(char_mode))
         lib().orc_set_tan_mode(self._h, int(tan_mode))
+        if lib().orc_set_coef_mode(self._h, int(coef_mode)) != 0:
+            lib().orc_destroy(self._h)
+            self._h = None
+            raise ValueError("coef_mode must be 0 or 1; 1 needs mu = 0 and tau_mode 0")
         wt = np.ascontiguousarray(wall_T, dtype=np.float64)
         wu = np.ascontiguousarray(wall_u, dtype=np.float64)
         if lib().orc_set_walls(self._h, _p(wt), _p(wu)) != 0:

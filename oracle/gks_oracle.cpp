@@ -53,7 +53,13 @@
 //       [0, dt] and fitted by a linear function of t (flux_mode = 0).
 //       flux_mode = 1 fits the whole time-integrated flux linearly.
 //   R6  the simplified coefficients a_t, a_xt, a_yt, a_tt lie in span(psi) and are
-//       fixed by the linearised compatibility chain.
+//       fixed by the linearised compatibility chain.  coef_mode = 1 (the full-product
+//       variant): the equilibrium is the second-order Taylor polynomial of the local
+//       Maxwellian, g0 [1 + a1 x + a2 y + A t + (a_xx + a1^2) x^2/2 + (a_xy + a1 a2) x y
+//       + (a_yy + a2^2) y^2/2 + (a_xt + a1 A) x t + (a_yt + a2 A) y t + (a_tt + A^2) t^2/2],
+//       whose psi-moments are W and its derivatives; the coefficients follow from those
+//       moments and the compatibility condition order by order, products included.  Only
+//       without the Chapman-Enskog bracket (mu = 0, tau_mode 0).
 //   R7  non-equilibrium slopes: WENO-weighted candidate derivatives (w1 quadratic).
 //   R8  WENO in the characteristic variables of the normal Jacobian at the mean of
 //       the two cells adjacent to the interface (char_mode = 1: component-wise instead,
@@ -581,6 +587,7 @@ struct Phys {
   int dim; double gamma, K, mu, Pr;
   double eps_tau = 0.01, C_tau = 1.0;
   int tau_mode = 0, flux_mode = 0, eq_mode = 1;
+  int coef_mode = 0;   // R6: 0 = simplified (linearised) coefficients, 1 = full products
 };
 
 bool primitives(const Phys& ph, const double* W, Maxw& g) {
@@ -646,10 +653,46 @@ bool gks_point(const Phys& ph, const PointIn& in, double dt, PointOut& out) {
     solve_coef(g0, res_moments, res_coef);
   };
   double Wt[4], A[4], Wxt[4], axt[4], Wyt[4], ayt[4] = {0, 0, 0, 0}, Wtt[4], att[4];
-  chain(a1, a2, Wt, A);
-  chain(axx, axy, Wxt, axt);
-  if (dim == 2) chain(axy, ayy, Wyt, ayt);
-  chain(axt, ayt, Wtt, att);
+  // full-product variant: the products of first-order coefficients in the Taylor terms
+  Poly Pxt, Pyt, Ptt;   // a_xt + a1 A, a_yt + a2 A, a_tt + A^2 (set below)
+  if (ph.coef_mode == 1) {
+    Poly L1 = lin(dim, a1), L2 = lin(dim, a2);
+    // second-order spatial coefficients: <psi (a_xx + a1^2) g0> = W_xx, ...
+    auto second = [&](const Poly& prod, const double* Wd, double* coef) {
+      double m[4], rhs[4];
+      momvec(prod, g0, SP_FULL, m);
+      for (int k = 0; k < n; ++k) rhs[k] = Wd[k] - m[k];
+      solve_coef(g0, rhs, coef);
+    };
+    second(pmul(L1, L1), in.W0xx, axx);
+    if (dim == 2) { second(pmul(L1, L2), in.W0xy, axy); second(pmul(L2, L2), in.W0yy, ayy); }
+    chain(a1, a2, Wt, A);   // first order: as in the simplified reading
+    Poly LA = lin(dim, A);
+    Poly Sxx = padd(lin(dim, axx), pmul(L1, L1));
+    Poly Sxy = padd(lin(dim, axy), pmul(L1, L2));
+    Poly Syy = padd(lin(dim, ayy), pmul(L2, L2));
+    // order x: <psi [(a_xt + a1 A) + u (a_xx + a1^2) + v (a_xy + a1 a2)] g0> = 0, and
+    // W_xt = <psi (a_xt + a1 A) g0>; likewise y; then order t for a_tt + A^2
+    auto mixed = [&](const Poly& su, const Poly& sv, const Poly& prod, double* Wd, double* coef,
+                     Poly& total) {
+      Poly P = pmul(U1, su);
+      if (dim == 2) P = padd(P, pmul(V1, sv));
+      double m[4], mp[4], rhs[4];
+      momvec(P, g0, SP_FULL, m);
+      momvec(prod, g0, SP_FULL, mp);
+      for (int k = 0; k < n; ++k) { Wd[k] = -m[k]; rhs[k] = -m[k] - mp[k]; }
+      solve_coef(g0, rhs, coef);
+      total = padd(lin(dim, coef), prod);
+    };
+    mixed(Sxx, Sxy, pmul(L1, LA), Wxt, axt, Pxt);
+    if (dim == 2) mixed(Sxy, Syy, pmul(L2, LA), Wyt, ayt, Pyt);
+    mixed(Pxt, Pyt, pmul(LA, LA), Wtt, att, Ptt);
+  } else {
+    chain(a1, a2, Wt, A);
+    chain(axx, axy, Wxt, axt);
+    if (dim == 2) chain(axy, ayy, Wyt, ayt);
+    chain(axt, ayt, Wtt, att);
+  }
 
   // Collision times (Sec. 4; reading R1).
   double p0 = pressure(g0), pl = pressure(gl), pr = pressure(gr);
@@ -657,6 +700,7 @@ bool gks_point(const Phys& ph, const PointIn& in, double dt, PointOut& out) {
   double tau_phys = ph.mu / p0;
   double tau_n = (ph.mu > 0.0 ? tau_phys : ph.eps_tau * dt) + jump;
   double tau_b = ph.tau_mode == 1 ? tau_n : tau_phys;
+  if (ph.coef_mode == 1 && tau_b > 0.0) return false;   // the variant has no bracket
 
   // Equilibrium branch of f: g0 [1 + A t + a_tt t^2/2] - tau_b g0 [(a1 u + a2 v + A) + (a_xt u + a_yt v + a_tt) t]
   Poly S1 = padd(pmul(U1, lin(dim, a1)), lin(dim, A));
@@ -666,7 +710,8 @@ bool gks_point(const Phys& ph, const PointIn& in, double dt, PointOut& out) {
   double fe0[4], fe1[4], fe2[4], fb1[4], fb2[4];
   momvec(U1, g0, SP_FULL, fe0);                       // int u psi g0
   momvec(pmul(U1, lin(dim, A)), g0, SP_FULL, fe1);    // int u psi A g0
-  momvec(pmul(U1, lin(dim, att)), g0, SP_FULL, fe2);  // int u psi a_tt g0
+  // int u psi a_tt g0 (full products: int u psi (a_tt + A^2) g0)
+  momvec(pmul(U1, ph.coef_mode == 1 ? Ptt : lin(dim, att)), g0, SP_FULL, fe2);
   momvec(pmul(U1, S1), g0, SP_FULL, fb1);
   momvec(pmul(U1, S2), g0, SP_FULL, fb2);
 
@@ -1266,10 +1311,10 @@ void orc_eigvecs(int dim, double gamma, const double* W, double* R) { euler_righ
 // One interface point: pin[12][4] in the order W0, W0x, W0y, W0xx, W0xy, W0yy, Wl, Wlx,
 // Wly, Wr, Wrx, Wry; out[5][4] = F, Ft, W0, Wt, Wtt.  Returns 0 or -4 (non-physical).
 int orc_point(int dim, double gamma, double mu, double Pr, int tau_mode, int flux_mode,
-              const double* pin, double dt, double* out) {
+              int coef_mode, const double* pin, double dt, double* out) {
   Phys ph; ph.dim = dim; ph.gamma = gamma; ph.mu = mu; ph.Pr = Pr;
   ph.K = dim == 1 ? (3.0 - gamma) / (gamma - 1.0) : (4.0 - 2.0 * gamma) / (gamma - 1.0);
-  ph.tau_mode = tau_mode; ph.flux_mode = flux_mode;
+  ph.tau_mode = tau_mode; ph.flux_mode = flux_mode; ph.coef_mode = coef_mode;
   PointIn in; std::memcpy(&in, pin, sizeof(in));
   PointOut po;
   if (!gks_point(ph, in, dt, po)) return -4;
@@ -1303,6 +1348,15 @@ void orc_destroy(void* h) { delete static_cast<Solver*>(h); }
 // Reading of the equilibrium interface value: 0 = linear compact reconstruction,
 // 1 = collision of the left/right initial states.
 void orc_set_eq_mode(void* h, int m) { static_cast<Solver*>(h)->ph.eq_mode = m; }
+// R6 option: 0 = simplified coefficients (default), 1 = full products; 1 needs mu = 0 and
+// tau_mode 0 (no Chapman-Enskog bracket).  Returns 0, or -1 (nothing set).
+int orc_set_coef_mode(void* h, int m) {
+  Solver* S = static_cast<Solver*>(h);
+  if (m != 0 && m != 1) return -1;
+  if (m == 1 && (S->ph.mu > 0.0 || S->ph.tau_mode != 0)) return -1;
+  S->ph.coef_mode = m;
+  return 0;
+}
 // R8 option: 0 = WENO-Z in characteristic variables (default), 1 = component-wise.
 void orc_set_char_mode(void* h, int m) { static_cast<Solver*>(h)->char_mode = m; }
 // Isothermal walls (bc 3, R25): T[4] wall temperatures p/rho and u[4] tangential wall

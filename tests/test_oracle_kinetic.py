@@ -197,6 +197,83 @@ def test_equilibrium_branch_matches_euler_derivatives(dim):
     np.testing.assert_allclose(out["Wtt"], Wtt, atol=1e-11)
 
 
+def _hess(W, dim, direction, u, v, eps=1e-5):
+    """(dA/dW . u) v, the flux Hessian contracted with u and v (central difference of the
+    complex-step Jacobian; error ~1e-10)."""
+    return (jacobian(W + eps * u, dim, direction) @ v - jacobian(W - eps * u, dim, direction) @ v) / (2 * eps)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_full_product_coefficients_give_the_cauchy_kowalewski_derivatives(dim):
+    """Reading R6, variant coef_mode = 1 (the second-order Taylor polynomial of the local
+    Maxwellian, products of first-order coefficients included): the interface values' time
+    derivatives are those of the Euler equations themselves, W_t = -(A W_x + B W_y) and
+    W_tt = -d/dt (A W_x + B W_y) = -(A W_xt + B W_yt + A'[W_t] W_x + B'[W_t] W_y) with
+    W_xt = -(A W_xx + B W_xy + A'[W_x] W_x + B'[W_x] W_y) and W_yt likewise (A'[u] the
+    Jacobian's derivative along u), while the simplified chain of the default reading lacks
+    the Jacobian-derivative terms; F and F_t are the same in both."""
+    rng = np.random.default_rng(11)
+    W0 = W_from_prim(1.1, 0.3, -0.5, 0.9, dim)
+    n = dim + 2
+    Wx, Wxx = rng.standard_normal(n) * 0.3, rng.standard_normal(n) * 0.3
+    Wy = rng.standard_normal(n) * 0.3 if dim == 2 else np.zeros(n)
+    Wxy = rng.standard_normal(n) * 0.3 if dim == 2 else np.zeros(n)
+    Wyy = rng.standard_normal(n) * 0.3 if dim == 2 else np.zeros(n)
+    f = _fields(dim, W0, Wx, Wxx, Wy if dim == 2 else None, Wxy if dim == 2 else None,
+                Wyy if dim == 2 else None)
+    full = oracle.point(dim, GAM, 0.0, 1.0, f, 1e-3, coef_mode=1)
+    simp = oracle.point(dim, GAM, 0.0, 1.0, f, 1e-3)
+    A = jacobian(W0, dim, 0)
+    B = jacobian(W0, dim, 1) if dim == 2 else np.zeros((n, n))
+    HA = lambda u, v: _hess(W0, dim, 0, u, v)   # noqa: E731
+    HB = (lambda u, v: _hess(W0, dim, 1, u, v)) if dim == 2 else (lambda u, v: np.zeros(n))  # noqa: E731
+    Wt = -(A @ Wx + B @ Wy)
+    Wxt = -(A @ Wxx + B @ Wxy + HA(Wx, Wx) + HB(Wx, Wy))
+    Wyt = -(A @ Wxy + B @ Wyy + HA(Wx, Wy) + HB(Wy, Wy))
+    Wtt = -(A @ Wxt + B @ Wyt + HA(Wt, Wx) + HB(Wt, Wy))
+    np.testing.assert_allclose(full["Wt"], Wt, atol=1e-12)
+    np.testing.assert_allclose(full["Wtt"], Wtt, atol=1e-8)
+    np.testing.assert_allclose(full["F"], simp["F"], atol=1e-14)
+    np.testing.assert_allclose(full["Ft"], simp["Ft"], atol=1e-13)
+    assert np.abs(simp["Wtt"] - Wtt).max() > 1e-3 * np.abs(Wtt).max()
+
+
+def _d4(fun, x, h):
+    """Fourth-order central first derivative."""
+    return (-fun(x + 2 * h) + 8 * fun(x + h) - 8 * fun(x - h) + fun(x - 2 * h)) / (12 * h)
+
+
+def test_full_product_interface_values_of_the_translating_vortex():
+    """The isentropic vortex translating at (1, 1) is an exact Euler solution, W(x, y, t) =
+    W(x - t, y - t, 0), so W_t = -(W_x + W_y) and W_tt = (d/dx + d/dy)^2 W exactly.  With the
+    point values and derivatives of the vortex (fourth-order differences), the full-product
+    variant gives both; the simplified chain misses W_tt by more than its size."""
+    from paper_1901_00261_gb300 import inputs
+    Wf = lambda x, y: inputs.vortex_point(np.array(x), np.array(y), 0.0, GAM)   # noqa: E731
+    x0, y0, h = 5.7, 4.6, 1e-3
+    dx = lambda F: (lambda x, y: _d4(lambda s: F(s, y), x, h))   # noqa: E731
+    dy = lambda F: (lambda x, y: _d4(lambda s: F(x, s), y, h))   # noqa: E731
+    Wx, Wy = dx(Wf), dy(Wf)
+    W, Wxv, Wyv = Wf(x0, y0), Wx(x0, y0), Wy(x0, y0)
+    Wxx, Wxy, Wyy = dx(Wx)(x0, y0), dy(Wx)(x0, y0), dy(Wy)(x0, y0)
+    f = dict(W0=W, W0x=Wxv, W0y=Wyv, W0xx=Wxx, W0xy=Wxy, W0yy=Wyy, Wl=W, Wr=W, Wlx=Wxv,
+             Wrx=Wxv, Wly=Wyv, Wry=Wyv)
+    exact_tt = Wxx + 2 * Wxy + Wyy
+    full = oracle.point(2, GAM, 0.0, 1.0, f, 1e-3, coef_mode=1)
+    simp = oracle.point(2, GAM, 0.0, 1.0, f, 1e-3)
+    np.testing.assert_allclose(full["Wt"], -(Wxv + Wyv), atol=1e-9)
+    np.testing.assert_allclose(full["Wtt"], exact_tt, atol=1e-7 * np.abs(exact_tt).max())
+    assert np.abs(simp["Wtt"] - exact_tt).max() > np.abs(exact_tt).max()
+
+
+def test_full_product_variant_needs_the_euler_bracket_free_setting():
+    with pytest.raises(ValueError):
+        oracle.Solver(10, 1, mu=0.01, coef_mode=1)
+    with pytest.raises(ValueError):
+        oracle.Solver(10, 1, tau_mode=1, coef_mode=1)
+    oracle.Solver(10, 1, coef_mode=1)
+
+
 @pytest.mark.parametrize("dim,Pr", [(1, 1.0), (1, 0.72), (2, 1.0), (2, 0.72)])
 def test_chapman_enskog_bracket_is_navier_stokes(dim, Pr):
     """With tau = mu/p (reading R1) the bracket of Eq. (3rd-simplify-flux) yields the

@@ -225,6 +225,36 @@ def test_isentropic_vortex_converges():
     assert math.log2(errs[0] / errs[1]) > 4.0, errs
 
 
+def _vortex_l1(n, order, T, **kw):
+    st = inputs.isentropic_vortex_2d(n, order=order, recon=0)
+    S = oracle.Solver(n, n, order=order, recon=0, x0=0, x1=10, y0=0, y1=10, **kw)
+    S.set_state(st.W, st.Wx, st.Wy)
+    ns = math.ceil(T / (0.3 / S.max_wavespeed()))
+    for _ in range(ns):
+        S.step(T / ns)
+    return np.abs(S.get_state()[0][0] - inputs.vortex_exact_avg(n, T)[0]).mean()
+
+
+def test_coefficient_reading_tables_cannot_tell_and_the_vortex_can():
+    """Reading R6: the full-product Taylor coefficients (coef_mode = 1) and the simplified
+    ones of the default reading give the same accuracy-table rows (the density wave has
+    uniform velocity and pressure, so the product terms nearly vanish): Table 1 at N = 40 to
+    4 digits.  On the isentropic vortex, a nonlinear flow, the full products are the more
+    accurate (64 x 64 at t = 1, 8th order: 2.3e-7 against 5.7e-7; 32 x 32 to t = 0.5 here)."""
+    a = run_density_wave(40, 6, 0)[0]
+    S = oracle.Solver(40, 1, order=6, recon=0, x0=0.0, x1=2.0, coef_mode=1)
+    st = inputs.density_wave_1d(40, order=6, recon=0)
+    S.set_state(st.W, st.Wx)
+    n = math.ceil(2.0 / (0.3 * (2.0 / 40) ** 1.5))
+    for _ in range(n):
+        S.step(2.0 / n)
+    b = np.abs(S.get_state()[0][0, 0] - inputs.density_wave_exact_rho(40, 2.0)).mean()
+    assert abs(b / a - 1) < 1e-4
+    simp = _vortex_l1(32, 8, 0.5)
+    full = _vortex_l1(32, 8, 0.5, coef_mode=1)
+    assert full < 0.8 * simp, (full, simp)   # 4.7e-6 against 6.6e-6
+
+
 def test_isentropic_vortex_converges_with_wenoz():
     """The same vortex with the compact WENO-Z reconstruction (8th-order linear weights): on
     smooth data the nonlinear weights approach the linear ones, so the error falls at high
