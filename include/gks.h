@@ -93,11 +93,18 @@ typedef struct gks_opts {
                               y walls: the x velocity; unused in 1D).  A moving isothermal
                               wall may not meet a GKS_BC_REFLECTING one (GKS_EINVAL): the
                               mirror image of a moving wall moves the other way */
+  int coef_mode;           /* equilibrium Taylor coefficients of Eq. 3rd-simplify-flux (Sec. 2.1):
+                              0 (default) the simplified coefficients a_t, a_xt, a_yt, a_tt of
+                              the linearised compatibility chain; 1 the full second-order
+                              Taylor polynomial of the local Maxwellian (products of the
+                              first-order coefficients kept), whose interface values' time
+                              derivatives are the Euler equations' own; FP64 form, mu = 0,
+                              tau_mode 0 and tan_mode 0 only (GKS_EINVAL otherwise) */
 } gks_opts;
 
 /* Fill *o with the defaults: domain [0,1] x [0,1], periodic, FP64, eps 1e-6,
  * eps_tau 0.01, C_tau 1, use_graph 1, tau_mode 0, stream NULL, tan_mode 0, wall_T 1,
- * wall_u 0. */
+ * wall_u 0, coef_mode 0. */
 void gks_default_opts(gks_opts* o);
 
 /* Create a solver for nx x ny cells (ny == 1: 1D).  gamma > 1 is the specific-heat ratio

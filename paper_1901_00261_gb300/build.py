@@ -15,9 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks_gb300.so")
-SOURCES = ["gks_faces.cu", "gks_faces32.cu", "gks_faces32_o8.cu", "gks_update.cu", "gks_api.cu", "gks_probe.cu", "gks_static.cu", "gks_batch.cu",
+SOURCES = ["gks_faces.cu", "gks_faces_o8.cu", "gks_faces_cm.cu", "gks_faces32.cu", "gks_faces32_o8.cu", "gks_update.cu", "gks_api.cu", "gks_probe.cu", "gks_static.cu", "gks_batch.cu",
            "gks_batch_k1.cu", "gks_batch_k2.cu", "gks_batch_k4.cu", "gks_batch_w1.cu", "gks_batch_w2.cu", "gks_batch_w4.cu"]
-HEADERS = ["gks_device.cuh", "gks_kernels.cuh", "gks_sweep.cuh", "gks_sweep32.cuh", "gks_batch.cuh", "gks_faces32_2d.cuh"]
+HEADERS = ["gks_device.cuh", "gks_faces.cuh", "gks_kernels.cuh", "gks_sweep.cuh", "gks_sweep32.cuh", "gks_batch.cuh", "gks_faces32_2d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-Xptxas", "-warn-spills"]

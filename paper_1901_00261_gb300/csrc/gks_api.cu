@@ -211,6 +211,7 @@ void gks_default_opts(gks_opts* o) {
   o->tan_mode = 0;
   o->stream = nullptr;
   for (int k = 0; k < 4; ++k) { o->wall_T[k] = 1.0; o->wall_u[k] = 0.0; }
+  o->coef_mode = 0;
 }
 
 const char* gks_last_error(void) { return g_err.c_str(); }
@@ -246,6 +247,10 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   if (!(o.weno_eps > 0.0) || !(o.eps_tau > 0.0) || !(o.C_tau >= 0.0)) { fail(GKS_EINVAL, "weno_eps, eps_tau must be > 0 and C_tau >= 0%s"); return nullptr; }
   if (o.tau_mode != 0 && o.tau_mode != 1) { fail(GKS_EINVAL, "tau_mode must be 0 or 1%s"); return nullptr; }
   if (o.tan_mode != 0 && o.tan_mode != 1) { fail(GKS_EINVAL, "tan_mode must be 0 or 1%s"); return nullptr; }
+  if (o.coef_mode != 0 && o.coef_mode != 1) { fail(GKS_EINVAL, "coef_mode must be 0 or 1%s"); return nullptr; }
+  if (o.coef_mode == 1 && (o.precision != GKS_PREC_FP64 || mu > 0.0 || o.tau_mode != 0 || o.tan_mode != 0)) {
+    fail(GKS_EINVAL, "coef_mode 1 needs the FP64 form, mu = 0, tau_mode 0 and tan_mode 0%s"); return nullptr;
+  }
 
   gks_ctx* c = new (std::nothrow) gks_ctx();
   if (!c) { fail(GKS_ENOMEM, "host allocation failed%s"); return nullptr; }
@@ -260,6 +265,7 @@ gks_ctx* gks_create(int nx, int ny, double gamma, double mu, double Pr, int orde
   c->P.eps_tau = o.eps_tau; c->P.C_tau = o.C_tau; c->P.weno_eps = o.weno_eps;
   c->P.tau_mode = o.tau_mode;
   c->P.tan_mode = o.tan_mode;
+  c->P.coef_mode = o.coef_mode;
   gks::set_phys_floats(c->P);
 
   cudaError_t e;

@@ -422,6 +422,8 @@ struct PhysParams {
   double gamma, K, mu, Pr, eps_tau, C_tau, weno_eps;
   float gammaf, Kf;   // single-precision copies of gamma and K (set with set_phys_floats)
   int tau_mode = 0;   // 0: bracket with mu/p (reading R1); 1: bracket with the numerical time
+  int coef_mode = 0;  // equilibrium Taylor coefficients: 0 simplified (linearised chain); 1 full
+                      // products (FP64 form, Euler; kernels instantiated with CM = true)
   int tan_mode = 0;   // 2D WENO-Z: 0 tangential quartic for every face quantity; 1 tangential
                       // WENO-Z for the non-equilibrium states (tan_weno)
 };
@@ -546,6 +548,35 @@ __device__ __forceinline__ void neg_div(const Flow<R, DIM>& f, const R* x, const
   }
 }
 
+// Second derivatives of the Euler fluxes contracted with two perturbations u, v of the
+// conservative variables: oF = (dA/dW . u) v for the normal flux, oG = (dB/dW . u) v for the
+// tangential one (2D), from the flux components m U + p, n U, (E + p) U (normal) and m V,
+// n V + p, (E + p) V (tangential) with U = m / rho, V = n / rho and
+// p = (gamma - 1)(E - (m^2 + n^2) / (2 rho)):
+//   d2U[u, v] = -(u_rho dU[v] + v_rho dU[u]) / rho,   d2p[u, v] = -(gamma - 1) rho (dU[u] dU[v] + dV[u] dV[v]).
+template <typename R, int DIM>
+__device__ __forceinline__ void euler_hess(const Flow<R, DIM>& f, const R* u, const R* v, R* oF, R* oG) {
+  const int N = DIM + 2;
+  const R uU = (u[1] - f.U * u[0]) * f.irho, vU = (v[1] - f.U * v[0]) * f.irho;
+  const R uV = DIM == 2 ? (u[2] - f.V * u[0]) * f.irho : R(0), vV = DIM == 2 ? (v[2] - f.V * v[0]) * f.irho : R(0);
+  const R up = f.g1 * (u[N - 1] - f.U * u[1] - (DIM == 2 ? f.V * u[2] : R(0)) + f.q2h * u[0]);
+  const R vp = f.g1 * (v[N - 1] - f.U * v[1] - (DIM == 2 ? f.V * v[2] : R(0)) + f.q2h * v[0]);
+  const R d2U = -(u[0] * vU + v[0] * uU) * f.irho;
+  const R d2V = DIM == 2 ? -(u[0] * vV + v[0] * uV) * f.irho : R(0);
+  const R d2p = -f.g1 * f.rho * (uU * vU + uV * vV);
+  const R m = f.rho * f.U, n = f.rho * f.V, Ep = f.rho * f.H;
+  oF[0] = R(0);
+  oF[1] = u[1] * vU + v[1] * uU + m * d2U + d2p;
+  if (DIM == 2) oF[2] = u[2] * vU + v[2] * uU + n * d2U;
+  oF[N - 1] = (u[N - 1] + up) * vU + (v[N - 1] + vp) * uU + Ep * d2U + f.U * d2p;
+  if (DIM == 2) {
+    oG[0] = R(0);
+    oG[1] = u[1] * vV + v[1] * uV + m * d2V;
+    oG[2] = u[2] * vV + v[2] * uV + n * d2V + d2p;
+    oG[3] = (u[3] + up) * vV + (v[3] + vp) * uV + Ep * d2V + f.V * d2p;
+  }
+}
+
 // Change of the Euler flux (normal direction) between the reference state r and r + d,
 // F(r + d) - F(r), written so that every term is a product with a component of d: in
 // single precision its error is relative to the change, not to the flux.
@@ -575,7 +606,9 @@ __device__ __forceinline__ void euler_flux_delta(const R* r, const R* d, R gamma
 // NEED_F = false (used by the second MSMD stage, which needs only F_t and W_tt): the flux and
 // interface-value outputs F, W0 and the flux half of the bracket and of the non-equilibrium
 // branch are not computed (out.F = out.W0 = 0).
-template <typename R, int DIM, bool WENO, bool VISC, bool DELTA = false, bool NEED_F = true>
+// CM: the full-product equilibrium coefficients (coef_mode 1; Euler only, VISC false): the
+// chain below gains the Euler fluxes' second-derivative terms.
+template <typename R, int DIM, bool WENO, bool VISC, bool DELTA = false, bool NEED_F = true, bool CM = false>
 __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, DIM>& in, double dt,
                                           PointOut<R, DIM>& out, const R* ref = nullptr,
                                           const R* d0 = nullptr) {
@@ -624,7 +657,35 @@ __device__ __forceinline__ bool gks_point(const PhysParams& P, const PointIn<R, 
   neg_div<R, DIM>(f, in.W0x, in.W0y, Wt);
   neg_div<R, DIM>(f, in.W0xx, in.W0xy, Wxt);
   if (DIM == 2) neg_div<R, DIM>(f, in.W0xy, in.W0yy, Wyt);
+  if constexpr (CM) {
+    // the Cauchy-Kowalewski derivatives of the Euler equations:
+    // W_xt = -(A W_xx + B W_xy + A'[W_x] W_x + B'[W_x] W_y), W_yt likewise
+    static_assert(!VISC, "the full-product coefficients are defined without the bracket");
+    R hF[N], hG[N];
+    euler_hess<R, DIM>(f, in.W0x, in.W0x, hF, hG);
+#pragma unroll
+    for (int k = 0; k < N; ++k) Wxt[k] -= hF[k];
+    if (DIM == 2) {
+      // A'[W_y] W_x = A'[W_x] W_y (the Hessian is symmetric)
+      R hyF[N], hyG[N];
+      euler_hess<R, DIM>(f, in.W0x, in.W0y, hF, hG);
+      euler_hess<R, DIM>(f, in.W0y, in.W0y, hyF, hyG);
+#pragma unroll
+      for (int k = 0; k < N; ++k) { Wxt[k] -= hG[k]; Wyt[k] -= hF[k] + hyG[k]; }
+    }
+  }
   neg_div<R, DIM>(f, Wxt, Wyt, Wtt);
+  if constexpr (CM) {   // W_tt = -(A W_xt + B W_yt + A'[W_t] W_x + B'[W_t] W_y)
+    R hF[N], hG[N];
+    euler_hess<R, DIM>(f, Wt, in.W0x, hF, hG);
+#pragma unroll
+    for (int k = 0; k < N; ++k) Wtt[k] -= hF[k];
+    if (DIM == 2) {
+      euler_hess<R, DIM>(f, Wt, in.W0y, hF, hG);
+#pragma unroll
+      for (int k = 0; k < N; ++k) Wtt[k] -= hG[k];
+    }
+  }
   jac_n<R, DIM>(f, Wt, Ft);
 
   if (VISC || WENO) {

@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
                 ("tau_mode", ctypes.c_int),
                 ("stream", ctypes.c_void_p),
                 ("tan_mode", ctypes.c_int),
-                ("wall_T", ctypes.c_double * 4), ("wall_u", ctypes.c_double * 4)]
+                ("wall_T", ctypes.c_double * 4), ("wall_u", ctypes.c_double * 4),
+                ("coef_mode", ctypes.c_int)]
 
 
 # Every symbol include/gks.h declares, with (restype, argtypes).
@@ -162,7 +163,7 @@ class Solver:
                  weno_eps: float = 1e-6, use_graph: bool = True, stream=None,
                  precision: int = PREC_FP64, tau_mode: int = 0, eps_tau: float = 0.01,
                  C_tau: float = 1.0, tan_mode: int = 0, wall_T=(1.0, 1.0, 1.0, 1.0),
-                 wall_u=(0.0, 0.0, 0.0, 0.0)):
+                 wall_u=(0.0, 0.0, 0.0, 0.0), coef_mode: int = 0):
         L = lib()
         o = default_opts()
         o.precision = precision
@@ -172,6 +173,7 @@ class Solver:
         o.use_graph = 1 if use_graph else 0
         o.tau_mode = tau_mode
         o.tan_mode = tan_mode
+        o.coef_mode = coef_mode
         for k in range(4):
             o.wall_T[k], o.wall_u[k] = float(wall_T[k]), float(wall_u[k])
         o.eps_tau, o.C_tau = eps_tau, C_tau

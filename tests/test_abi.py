@@ -38,7 +38,7 @@ def test_default_opts():
     assert (o.x0, o.x1, o.bc_x, o.weno_eps, o.eps_tau, o.C_tau, o.use_graph) == (0.0, 1.0, 0, 1e-6, 0.01, 1.0, 1)
     assert o.tau_mode == 0 and o.stream is None and o.tan_mode == 0
     # the last fields: a layout mismatch between the header and the binding shows here
-    assert list(o.wall_T) == [1.0] * 4 and list(o.wall_u) == [0.0] * 4
+    assert list(o.wall_T) == [1.0] * 4 and list(o.wall_u) == [0.0] * 4 and o.coef_mode == 0
 
 
 @pytest.mark.parametrize("change,msg", [
@@ -47,6 +47,9 @@ def test_default_opts():
     (dict(bc_y=3, wall_T=(1.0, 1.0, 0.0, 1.0)), "wall_T"),
     (dict(bc_x=3, wall_u=(0.0, float("nan"), 0.0, 0.0)), "wall_u"),
     (dict(bc_x=2, bc_y=3, wall_u=(0.0, 0.0, 0.0, 0.1)), "reflecting"),
+    (dict(coef_mode=2), "coef_mode"),
+    (dict(coef_mode=1, precision=1), "coef_mode 1"),
+    (dict(coef_mode=1, tau_mode=1), "coef_mode 1"),
 ])
 def test_create_rejects_invalid_walls(change, msg):
     L = gks.lib()

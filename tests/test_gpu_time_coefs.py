@@ -126,7 +126,8 @@ def test_d2f_rounds_to_nearest_even():
             np.inf, -np.inf, 1.0, -1.0, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 0.1, 1.0 / 3.0]
     xs = np.concatenate([x, ties, -ties, np.array(edge)])
     got = gks.probe_d2f(xs)
-    want = xs.astype(np.float32)
+    with np.errstate(over="ignore"):   # values beyond the float range round to inf
+        want = xs.astype(np.float32)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
     nan = gks.probe_d2f(np.array([np.nan]))
     assert np.isnan(nan[0])
