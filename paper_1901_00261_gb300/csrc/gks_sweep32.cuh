@@ -124,6 +124,22 @@ __device__ __forceinline__ void swap_uv_f(float* w) {
 // same persistent launch by other blocks (L1 is not coherent across SMs).
 template <bool CG>
 __device__ __forceinline__ float ldf(const float* p) { return CG ? __ldcg(p) : *p; }
+// one 128-bit load of the four variables of a 2D mirror cell
+template <bool CG>
+__device__ __forceinline__ float4 ldf4(const float* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  return CG ? __ldcg(q) : *q;
+}
+__device__ __forceinline__ void unpack4(const float4 a, float* o) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
+
+// Layout of the FP32 mirror (blocks q = 0 hi, 1 lo, 2 x slope, 3 y slope): in 2D each block
+// is cell-major, the four variables of a cell one float4 (index 4 (q ncell + c) + v), so a
+// cell's block is one 128-bit access; in 1D each block is three planes (index
+// (3 q + v) ncell + c).  In both, block q starts at q N ncell.
+template <int DIM>
+__device__ __forceinline__ long mirror_at(int q, int v, long c, long ncell) {
+  return DIM == 2 ? 4 * ((long)q * ncell + c) + v : ((long)q * 3 + v) * ncell + c;
+}
 template <bool CG>
 __device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
 
@@ -350,8 +366,8 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
       long cr;
       if (DIR == 0) cr = (long)ct * a.nx + map_index<WALLS>(fn - 1, a.nx, a.bcx);
       else cr = (long)map_index<WALLS>(fn - 1, a.ny, a.bcy) * a.nx + ct;
-#pragma unroll
-      for (int v = 0; v < N; ++v) { ref[v] = ldf<CG>(a.M + v * ncell + cr); rlo[v] = ldf<CG>(a.M + L + v * ncell + cr); }
+      unpack4(ldf4<CG>(a.M + 4 * cr), ref);
+      unpack4(ldf4<CG>(a.M + 4 * (ncell + cr)), rlo);
       if (walls) mirror_ghost<2, DIR, float>(ref, rlo, nullptr, beyond_wall(fn - 1, nnc, bcn), rt);
       if (DIR == 1) { swap_uv_f<2>(ref); swap_uv_f<2>(rlo); }
       float in[N][8];
@@ -363,12 +379,14 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
         // cell o = 1 is the reference cell itself (same index map and mirror): its
         // difference from the reference is zero and only its slope is loaded
         float hi[N], lo[N], g[N];
+        if (o != 1) {
+          unpack4(ldf4<CG>(a.M + 4 * c), hi);
+          unpack4(ldf4<CG>(a.M + 4 * (ncell + c)), lo);
+        } else {
 #pragma unroll
-        for (int v = 0; v < N; ++v) {
-          if (o != 1) { hi[v] = ldf<CG>(a.M + v * ncell + c); lo[v] = ldf<CG>(a.M + L + v * ncell + c); }
-          else { hi[v] = 0.f; lo[v] = 0.f; }
-          g[v] = ldf<CG>(a.Mn + v * ncell + c);
+          for (int v = 0; v < N; ++v) { hi[v] = 0.f; lo[v] = 0.f; }
         }
+        unpack4(ldf4<CG>(a.Mn + 4 * c), g);
         if (walls) mirror_ghost<2, DIR, float>(hi, lo, g, beyond_wall(fn - 2 + o, nnc, bcn), rt);
         if (DIR == 1) { swap_uv_f<2>(hi); swap_uv_f<2>(lo); swap_uv_f<2>(g); }
 #pragma unroll
@@ -604,20 +622,38 @@ faces_2d_f32_kernel(FaceArgs32 a) {
 //     a run restarted from its FP64 state continues bit for bit.
 // ---------------------------------------------------------------------------
 // FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
+// Store one cell's mirror blocks (hi, lo, x slope, y slope; the y slope unused in 1D).
+template <int DIM>
+__device__ __forceinline__ void store_mirror(float* M, long c, long ncell, const float* hi,
+                                             const float* lo, const float* sx, const float* sy) {
+  if constexpr (DIM == 2) {
+    float4* M4 = reinterpret_cast<float4*>(M);
+    M4[c] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    M4[ncell + c] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    M4[2 * ncell + c] = make_float4(sx[0], sx[1], sx[2], sx[3]);
+    M4[3 * ncell + c] = make_float4(sy[0], sy[1], sy[2], sy[3]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) {
+      M[mirror_at<1>(0, v, c, ncell)] = hi[v];
+      M[mirror_at<1>(1, v, c, ncell)] = lo[v];
+      M[mirror_at<1>(2, v, c, ncell)] = sx[v];
+    }
+  }
+}
+
 template <int DIM>
 __device__ __forceinline__ void write_mirror(float* M, long c, long ncell, const double* w,
                                              const double* wx, const double* wy) {
   const int N = DIM + 2;
-  const long L = N * ncell;
+  float hi[N], lo[N], sx[N], sy[N];
 #pragma unroll
   for (int v = 0; v < N; ++v) {
-    float hi, lo;
-    split_hilo(w[v], hi, lo);
-    M[v * ncell + c] = hi;
-    M[L + v * ncell + c] = lo;
-    M[2 * L + v * ncell + c] = d2f_int(wx[v]);
-    if (DIM == 2) M[3 * L + v * ncell + c] = d2f_int(wy[v]);
+    split_hilo(w[v], hi[v], lo[v]);
+    sx[v] = d2f_int(wx[v]);
+    sy[v] = DIM == 2 ? d2f_int(wy[v]) : 0.f;
   }
+  store_mirror<DIM>(M, c, ncell, hi, lo, sx, sy);
 }
 
 // Cells [c0, c0 + n) of a state of ncell cells.
@@ -658,10 +694,15 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
     // all loads first
     float h0[N], lo0[N], Ax[N], Dxv[N], Ol[N], Or[N], dWx[N];
     float Ay[N], Dyv[N], Ob[N], Ot[N], dWy[N];
+    if constexpr (DIM == 2) {
+      unpack4(ldf4<false>(M + 4 * c), h0);
+      unpack4(ldf4<false>(M + 4 * (ncell + c)), lo0);
+    } else {
+#pragma unroll
+      for (int v = 0; v < N; ++v) { h0[v] = M[mirror_at<1>(0, v, c, ncell)]; lo0[v] = M[mirror_at<1>(1, v, c, ncell)]; }
+    }
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      h0[v] = M[v * ncell + c];
-      lo0[v] = M[L + v * ncell + c];
       Ol[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
       Or[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1);
       Ax[v] = ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1);
@@ -675,6 +716,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
         dWy[v] = (float)ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
       }
     }
+    float mh[N], ml[N], mx[N], my[N];   // the W* mirror of this cell
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       float inc = (Ax[v] + Dxv[v]) * idxf;   // (A_{i+1/2} + D_{i-1/2}) / dx
@@ -690,11 +732,12 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       const float bb = s1 - h0[v];
       const float lo = lo0[v] + ((h0[v] - (s1 - bb)) + (d - bb));
       const float hi = s1 + lo;
-      M[v * ncell + c] = hi;
-      M[L + v * ncell + c] = lo - (hi - s1);
-      M[2 * L + v * ncell + c] = wxs;
-      if (DIM == 2) M[3 * L + v * ncell + c] = wys;
+      mh[v] = hi;
+      ml[v] = lo - (hi - s1);
+      mx[v] = wxs;
+      my[v] = wys;
     }
+    store_mirror<DIM>(M, c, ncell, mh, ml, mx, my);
   } else {
     // all loads first, then the FP64 accumulation and the stores
     double W0[N], Xl[N], Xr[N], dWx[N], Yb[N], Yt[N], dWy[N];
@@ -713,6 +756,7 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
         dLy[v] = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
       }
     }
+    float mh[N], ml[N], mx[N], my[N];   // the W^{n+1} mirror of this cell
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       // the slopes (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2}) / dx in FP64, and their float
@@ -720,19 +764,18 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
       double w = W0[v] - (Xr[v] - Xl[v]) * idx;
       const double sx = fma(dWx[v], idx, f2d_int(dLx[v] * idxf));
       a.W[L + v * ncell + c] = sx;
-      M[2 * L + v * ncell + c] = d2f_int(sx);
+      mx[v] = d2f_int(sx);
+      my[v] = 0.f;
       if (DIM == 2) {
         w -= (Yt[v] - Yb[v]) * idy;
         const double sy = fma(dWy[v], idy, f2d_int(dLy[v] * idyf));
         a.W[2 * L + v * ncell + c] = sy;
-        M[3 * L + v * ncell + c] = d2f_int(sy);
+        my[v] = d2f_int(sy);
       }
       a.W[v * ncell + c] = w;
-      float hi, lo;
-      split_hilo(w, hi, lo);
-      M[v * ncell + c] = hi;
-      M[L + v * ncell + c] = lo;
+      split_hilo(w, mh[v], ml[v]);
     }
+    store_mirror<DIM>(M, c, ncell, mh, ml, mx, my);
   }
 }
 
