@@ -94,27 +94,6 @@ __device__ __forceinline__ void prefetch_line(const void* p) {
   else asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Start the epilogue's global reads of face `face` (stage 1: the FP64 states of its cells
-// cl, cr; stage 2: its FP64 flux part Xi and FP32 dLT) while the face is evaluated.
-template <int DIM, bool CG>
-__device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, int stage, long face, long nfaces,
-                                                       long cl, long cr) {
-  const int N = DIM + 2;
-  const long ncell = (long)a.nx * a.ny;
-  if (stage == 1) {
-#pragma unroll
-    for (int v = 0; v < N; ++v) { prefetch_line<CG>(a.W + v * ncell + cl); prefetch_line<CG>(a.W + v * ncell + cr); }
-  } else {
-    const double* o64 = static_cast<const double*>(a.out);
-    const float* o32 = reinterpret_cast<const float*>(o64 + 2L * N * nfaces);
-#pragma unroll
-    for (int v = 0; v < N; ++v) {
-      prefetch_line<CG>(o64 + (long)v * nfaces + face);
-      prefetch_line<CG>(o32 + (1L * N + v) * nfaces + face);
-    }
-  }
-}
-
 template <int DIM>
 __device__ __forceinline__ void swap_uv_f(float* w) {
   if (DIM == 2) { float t = w[1]; w[1] = w[2]; w[2] = t; }
@@ -124,6 +103,8 @@ __device__ __forceinline__ void swap_uv_f(float* w) {
 // same persistent launch by other blocks (L1 is not coherent across SMs).
 template <bool CG>
 __device__ __forceinline__ float ldf(const float* p) { return CG ? __ldcg(p) : *p; }
+template <bool CG>
+__device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
 // one 128-bit load of the four variables of a 2D mirror cell
 template <bool CG>
 __device__ __forceinline__ float4 ldf4(const float* p) {
@@ -140,8 +121,86 @@ template <int DIM>
 __device__ __forceinline__ long mirror_at(int q, int v, long c, long ncell) {
   return DIM == 2 ? 4 * ((long)q * ncell + c) + v : ((long)q * 3 + v) * ncell + c;
 }
-template <bool CG>
-__device__ __forceinline__ double ldd(const double* p) { return CG ? __ldcg(p) : *p; }
+
+// Face buffer of the FP32-bulk form: two FP64 blocks (k = 0 Xi, 1 dW), then four FP32 blocks
+// (q = 0 dOmega, 1 dLT, 2 A, 3 D), each nfaces long.  In 2D each block is face-major, a face's
+// four variables contiguous (two 128-bit accesses for the FP64 blocks, one for the FP32
+// ones); in 1D each block is three planes.
+template <int DIM, bool CG>
+__device__ __forceinline__ void ld_face64(const double* o64, int k, long face, long nfaces, double* v) {
+  if constexpr (DIM == 2) {
+    const double2* p = reinterpret_cast<const double2*>(o64) + 2 * ((long)k * nfaces + face);
+    const double2 a = CG ? __ldcg(p) : p[0], b = CG ? __ldcg(p + 1) : p[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = ldd<CG>(o64 + ((long)k * 3 + i) * nfaces + face);
+  }
+}
+template <int DIM>
+__device__ __forceinline__ void st_face64(double* o64, int k, long face, long nfaces, const double* v) {
+  if constexpr (DIM == 2) {
+    double2* p = reinterpret_cast<double2*>(o64) + 2 * ((long)k * nfaces + face);
+    p[0] = make_double2(v[0], v[1]);
+    p[1] = make_double2(v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o64[((long)k * 3 + i) * nfaces + face] = v[i];
+  }
+}
+template <int DIM, bool CG>
+__device__ __forceinline__ void ld_face32(const float* o32, int q, long face, long nfaces, float* v) {
+  if constexpr (DIM == 2) {
+    unpack4(ldf4<CG>(o32 + 4 * ((long)q * nfaces + face)), v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = ldf<CG>(o32 + ((long)q * 3 + i) * nfaces + face);
+  }
+}
+template <int DIM>
+__device__ __forceinline__ void st_face32(float* o32, int q, long face, long nfaces, const float* v) {
+  if constexpr (DIM == 2) {
+    reinterpret_cast<float4*>(o32)[(long)q * nfaces + face] = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o32[((long)q * 3 + i) * nfaces + face] = v[i];
+  }
+}
+template <int DIM>
+__device__ __forceinline__ long face64_at(int k, long face, long nfaces) {
+  return DIM == 2 ? 4 * ((long)k * nfaces + face) : (long)k * 3 * nfaces + face;
+}
+template <int DIM>
+__device__ __forceinline__ long face32_at(int q, long face, long nfaces) {
+  return DIM == 2 ? 4 * ((long)q * nfaces + face) : (long)q * 3 * nfaces + face;
+}
+
+// Start the epilogue's global reads of face `face` (stage 1: the FP64 states of its cells
+// cl, cr; stage 2: its FP64 flux part Xi and FP32 dLT) while the face is evaluated.
+template <int DIM, bool CG>
+__device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, int stage, long face, long nfaces,
+                                                       long cl, long cr) {
+  const int N = DIM + 2;
+  const long ncell = (long)a.nx * a.ny;
+  if (stage == 1) {
+#pragma unroll
+    for (int v = 0; v < N; ++v) { prefetch_line<CG>(a.W + v * ncell + cl); prefetch_line<CG>(a.W + v * ncell + cr); }
+  } else {
+    const double* o64 = static_cast<const double*>(a.out);
+    const float* o32 = reinterpret_cast<const float*>(o64 + 2L * N * nfaces);
+    if constexpr (DIM == 2) {   // a face's Xi and dLT lie in one line each
+      prefetch_line<CG>(o64 + face64_at<DIM>(0, face, nfaces));
+      prefetch_line<CG>(o32 + face32_at<DIM>(1, face, nfaces));
+    } else {
+#pragma unroll
+      for (int v = 0; v < N; ++v) {
+        prefetch_line<CG>(o64 + (long)v * nfaces + face);
+        prefetch_line<CG>(o32 + (1L * N + v) * nfaces + face);
+      }
+    }
+  }
+}
+
 
 // Normal Euler flux (global frame) of an FP64 state across a face of direction DIR.
 template <int DIM, int DIR>
@@ -157,7 +216,8 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
   F[N - 1] = (W[N - 1] + p) * un;
 }
 
-// Face outputs of the FP32-bulk sweeps.  The face buffer holds 2N FP64 planes, then FP32 planes:
+// Face outputs of the FP32-bulk sweeps.  The face buffer holds two FP64 blocks, then four FP32
+// blocks (layout at ld_face64: per face and block, the variables contiguous in 2D):
 //   FP64 Xi  = dt F_ref + (dt dF + dt^2/6 F_t)           (stage 1; stage 2 adds dt^2/3 F_t*)
 //   FP64 dW  = W_right - W_left of the face's two cells    (stage 1)
 //   FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt     (stage 1)
@@ -186,16 +246,19 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
   const int stage = STAGE ? STAGE : a.stage;
   if (stage == 1) {
     const float hf = ldf<CG>(&tc->hf), h2f = ldf<CG>(&tc->h2f), dtf = ldf<CG>(&tc->dtf), s6f = ldf<CG>(&tc->s6f);
-    float dpsi[N];
+    float dpsi[N], q0[N], q1[N], q2[N], q3[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      o32[(0L * N + v) * nfaces + face] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
-      o32[(1L * N + v) * nfaces + face] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
-      const float A = hf * F[v] + h2f * Ft[v];
-      o32[(2L * N + v) * nfaces + face] = A;
-      o32[(3L * N + v) * nfaces + face] = hf * dFc[v] - A;
+      q0[v] = dW0[v] + hf * Wt[v] + h2f * Wtt[v];
+      q1[v] = dW0[v] + dtf * Wt[v] + s6f * Wtt[v];
+      q2[v] = hf * F[v] + h2f * Ft[v];
+      q3[v] = hf * dFc[v] - q2[v];
       dpsi[v] = dtf * F[v] + s6f * Ft[v];
     }
+    st_face32<DIM>(o32, 0, face, nfaces, q0);
+    st_face32<DIM>(o32, 1, face, nfaces, q1);
+    st_face32<DIM>(o32, 2, face, nfaces, q2);
+    st_face32<DIM>(o32, 3, face, nfaces, q3);
     double wl[N], wr[N], Fref[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) { wl[v] = ldd<CG>(a.W + v * ncell + cl); wr[v] = ldd<CG>(a.W + v * ncell + cr); }
@@ -203,6 +266,7 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
     if (mr) wr[1 + DIR] = -wr[1 + DIR];
     euler_flux64<DIM, DIR>(wl, a.P.gamma, Fref);
     const double dt = ldd<CG>(&tc->dt);
+    double xi[N], dw[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       // at a wall face every flux but that of the wall-normal momentum is an odd function
@@ -210,18 +274,24 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
       // reference would leave ~1e-8 |rho U| instead, so the FP64 flux is set to zero there
       // (conservation of mass, energy and tangential momentum stays exact)
       const bool odd_at_wall = (ml || mr) && v != 1 + DIR;
-      o64[(long)v * nfaces + face] = odd_at_wall ? 0.0 : fma(dt, Fref[v], f2d_int(dpsi[v]));
-      o64[(long)(N + v) * nfaces + face] = wr[v] - wl[v];
+      xi[v] = odd_at_wall ? 0.0 : fma(dt, Fref[v], f2d_int(dpsi[v]));
+      dw[v] = wr[v] - wl[v];
     }
+    st_face64<DIM>(o64, 0, face, nfaces, xi);
+    st_face64<DIM>(o64, 1, face, nfaces, dw);
   } else {
     const float s3f = ldf<CG>(&tc->s3f);
+    double xi[N];
+    float lt[N];
+    ld_face64<DIM, CG>(o64, 0, face, nfaces, xi);
+    ld_face32<DIM, CG>(o32, 1, face, nfaces, lt);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      double* xi = o64 + (long)v * nfaces + face;
-      if (!((ml || mr) && v != 1 + DIR)) *xi = ldd<CG>(xi) + f2d_int(s3f * Ft[v]);
-      float* lt = o32 + (1L * N + v) * nfaces + face;
-      *lt = ldf<CG>(lt) + s3f * Wtt[v];
+      if (!((ml || mr) && v != 1 + DIR)) xi[v] += f2d_int(s3f * Ft[v]);
+      lt[v] += s3f * Wtt[v];
     }
+    st_face64<DIM>(o64, 0, face, nfaces, xi);
+    st_face32<DIM>(o32, 1, face, nfaces, lt);
   }
 }
 
@@ -345,7 +415,6 @@ __device__ __forceinline__ void sweep2d_f32_tile(const FaceArgs32& a, int bx, in
   float* sdfcp = sreflo + N * T::NS;
   const double dt = ldd<CG>(a.dtp);
   const long ncell = (long)a.nx * a.ny;
-  const long L = N * ncell;
   const int nthreads = TA32 * TB32;
   const int nn = DIR == 0 ? a.nx + 1 : a.ny + 1;
 
@@ -701,19 +770,23 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
 #pragma unroll
       for (int v = 0; v < N; ++v) { h0[v] = M[mirror_at<1>(0, v, c, ncell)]; lo0[v] = M[mirror_at<1>(1, v, c, ncell)]; }
     }
+    {
+      double d[N];
+      ld_face32<DIM, CG>(x32, 0, fxl, nfx, Ol);
+      ld_face32<DIM, CG>(x32, 0, fxl + 1, nfx, Or);
+      ld_face32<DIM, CG>(x32, 2, fxl + 1, nfx, Ax);
+      ld_face32<DIM, CG>(x32, 3, fxl, nfx, Dxv);
+      ld_face64<DIM, CG>(x64, 1, fxl, nfx, d);
 #pragma unroll
-    for (int v = 0; v < N; ++v) {
-      Ol[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl);
-      Or[v] = ldf<CG>(x32 + (0L * N + v) * nfx + fxl + 1);
-      Ax[v] = ldf<CG>(x32 + (2L * N + v) * nfx + fxl + 1);
-      Dxv[v] = ldf<CG>(x32 + (3L * N + v) * nfx + fxl);
-      dWx[v] = (float)ldd<CG>(x64 + (long)(N + v) * nfx + fxl);
+      for (int v = 0; v < N; ++v) dWx[v] = (float)d[v];
       if (DIM == 2) {
-        Ob[v] = ldf<CG>(y32 + (0L * N + v) * nfy + fyb);
-        Ot[v] = ldf<CG>(y32 + (0L * N + v) * nfy + fyt);
-        Ay[v] = ldf<CG>(y32 + (2L * N + v) * nfy + fyt);
-        Dyv[v] = ldf<CG>(y32 + (3L * N + v) * nfy + fyb);
-        dWy[v] = (float)ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
+        ld_face32<DIM, CG>(y32, 0, fyb, nfy, Ob);
+        ld_face32<DIM, CG>(y32, 0, fyt, nfy, Ot);
+        ld_face32<DIM, CG>(y32, 2, fyt, nfy, Ay);
+        ld_face32<DIM, CG>(y32, 3, fyb, nfy, Dyv);
+        ld_face64<DIM, CG>(y64, 1, fyb, nfy, d);
+#pragma unroll
+        for (int v = 0; v < N; ++v) dWy[v] = (float)d[v];
       }
     }
     float mh[N], ml[N], mx[N], my[N];   // the W* mirror of this cell
@@ -743,17 +816,24 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
     double W0[N], Xl[N], Xr[N], dWx[N], Yb[N], Yt[N], dWy[N];
     float dLx[N], dLy[N];
 #pragma unroll
-    for (int v = 0; v < N; ++v) {
-      W0[v] = ldd<CG>(a.W + v * ncell + c);
-      Xl[v] = ldd<CG>(x64 + (long)v * nfx + fxl);
-      Xr[v] = ldd<CG>(x64 + (long)v * nfx + fxl + 1);
-      dWx[v] = ldd<CG>(x64 + (long)(N + v) * nfx + fxl);
-      dLx[v] = ldf<CG>(x32 + (1L * N + v) * nfx + fxl + 1) - ldf<CG>(x32 + (1L * N + v) * nfx + fxl);
+    for (int v = 0; v < N; ++v) W0[v] = ldd<CG>(a.W + v * ncell + c);
+    {
+      float l0[N], l1[N];
+      ld_face64<DIM, CG>(x64, 0, fxl, nfx, Xl);
+      ld_face64<DIM, CG>(x64, 0, fxl + 1, nfx, Xr);
+      ld_face64<DIM, CG>(x64, 1, fxl, nfx, dWx);
+      ld_face32<DIM, CG>(x32, 1, fxl + 1, nfx, l1);
+      ld_face32<DIM, CG>(x32, 1, fxl, nfx, l0);
+#pragma unroll
+      for (int v = 0; v < N; ++v) dLx[v] = l1[v] - l0[v];
       if (DIM == 2) {
-        Yb[v] = ldd<CG>(y64 + (long)v * nfy + fyb);
-        Yt[v] = ldd<CG>(y64 + (long)v * nfy + fyt);
-        dWy[v] = ldd<CG>(y64 + (long)(N + v) * nfy + fyb);
-        dLy[v] = ldf<CG>(y32 + (1L * N + v) * nfy + fyt) - ldf<CG>(y32 + (1L * N + v) * nfy + fyb);
+        ld_face64<DIM, CG>(y64, 0, fyb, nfy, Yb);
+        ld_face64<DIM, CG>(y64, 0, fyt, nfy, Yt);
+        ld_face64<DIM, CG>(y64, 1, fyb, nfy, dWy);
+        ld_face32<DIM, CG>(y32, 1, fyt, nfy, l1);
+        ld_face32<DIM, CG>(y32, 1, fyb, nfy, l0);
+#pragma unroll
+        for (int v = 0; v < N; ++v) dLy[v] = l1[v] - l0[v];
       }
     }
     float mh[N], ml[N], mx[N], my[N];   // the W^{n+1} mirror of this cell
