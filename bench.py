@@ -54,24 +54,25 @@ CFL = 0.3
 # 20 %); traffic: DRAM bytes (read + write) per unit of a full-size launch (2048^2, one-pass
 # dram__bytes capture of the benchmark's own step), scaled by the units a launch processes.
 # The FP64 form has no traffic figure: its 256^2 capture fits in L2.  winstr: executed
-# warp-instructions per 32 units (the FP32-bulk stage-1 sweeps from a 1024^2 capture of the
-# current build, the FP64 sweeps from the 256^2 one), for the instruction-issue rate the
-# sweeps are limited by (reported beside the roofline).
+# warp-instructions per 32 units (same captures), for the instruction-issue rate the sweeps
+# are limited by (reported beside the roofline).
 KERNEL_MODEL = {
     ("linear_euler", "fp64", "x_faces_stage1"): {"unit": "face", "f64": 1961.2, "winstr": 7353},
     ("linear_euler", "fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
     ("linear_euler", "fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
     ("linear_euler", "fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
-    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 195.3,
-                                                 "winstr": 2134},
-    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 195.2,
-                                                 "winstr": 1978},
+    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 195.9,
+                                                 "winstr": 2071},
+    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 194.6,
+                                                 "winstr": 1922},
     ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0,
-                                                "traffic": 248.5},
-    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1826.6, "f64": 4.0, "traffic": 135.3},
-    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1750.0, "f64": 4.0, "traffic": 135.2},
+                                                "traffic": 248.3, "winstr": 244},
+    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1824.6, "f64": 4.0, "traffic": 134.3,
+                                                 "winstr": 1626},
+    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1747.0, "f64": 4.0, "traffic": 133.2,
+                                                 "winstr": 1483},
     ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0,
-                                                "traffic": 340.1},
+                                                "traffic": 340.0, "winstr": 676},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face and warp-instructions per
     # 32 faces from one-pass instruction-counter captures of the 4096^2 step (the FP64 count
