@@ -77,10 +77,10 @@ KERNEL_MODEL = {
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face and warp-instructions per
     # 32 faces from one-pass instruction-counter captures of the 4096^2 step (the FP64 count
     # depends on the grid through dt/tau: the time coefficients' series length follows it)
-    ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 10605.3, "f64": 238.3, "winstr": 9808},
-    ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10168.9, "f64": 238.3, "winstr": 9343},
-    ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 10041.3, "f64": 141.3, "winstr": 8782},
-    ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 9604.9, "f64": 141.3, "winstr": 8355},
+    ("wenoz_ns", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 10605.3, "f64": 238.3, "winstr": 9619},
+    ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10168.9, "f64": 238.3, "winstr": 9168},
+    ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 10041.3, "f64": 141.3, "winstr": 8601},
+    ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 9604.9, "f64": 141.3, "winstr": 8192},
     ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0},
     ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0},
 }
