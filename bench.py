@@ -61,18 +61,18 @@ KERNEL_MODEL = {
     ("linear_euler", "fp64", "y_faces_stage1"): {"unit": "face", "f64": 1809.6, "winstr": 5962},
     ("linear_euler", "fp64", "x_faces_stage2"): {"unit": "face", "f64": 1826.2, "winstr": 6914},
     ("linear_euler", "fp64", "y_faces_stage2"): {"unit": "face", "f64": 1674.6, "winstr": 5570},
-    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 195.9,
-                                                 "winstr": 2071},
-    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 194.6,
-                                                 "winstr": 1922},
-    ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0,
-                                                "traffic": 248.3, "winstr": 244},
-    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1824.6, "f64": 4.0, "traffic": 134.3,
+    ("linear_euler", "fp32", "x_faces_stage1"): {"unit": "face", "f32": 2129.1, "f64": 35.0, "traffic": 180.8,
+                                                 "winstr": 2092},
+    ("linear_euler", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 2052.5, "f64": 35.0, "traffic": 179.0,
+                                                 "winstr": 1941},
+    ("linear_euler", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 224.0,
+                                                "traffic": 213.6, "winstr": 251},
+    ("linear_euler", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 1824.6, "f64": 4.0, "traffic": 134.4,
                                                  "winstr": 1626},
-    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1747.0, "f64": 4.0, "traffic": 133.2,
+    ("linear_euler", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 1747.0, "f64": 4.0, "traffic": 133.3,
                                                  "winstr": 1483},
-    ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0,
-                                                "traffic": 340.0, "winstr": 676},
+    ("linear_euler", "fp32", "update_stage2"): {"unit": "cell", "f32": 44.0, "f64": 24.0, "bytes": 320.0,
+                                                "traffic": 309.2, "winstr": 608},
     # 8th-order WENO-Z Navier-Stokes sweeps (double shear layer), FP32-bulk form: executed
     # FFMA x 2 + FMUL + FADD (and DFMA x 2 + DMUL + DADD) per face and warp-instructions per
     # 32 faces from one-pass instruction-counter captures of the 4096^2 step (the FP64 count
@@ -81,8 +81,8 @@ KERNEL_MODEL = {
     ("wenoz_ns", "fp32", "y_faces_stage1"): {"unit": "face", "f32": 10168.9, "f64": 238.3, "winstr": 9168},
     ("wenoz_ns", "fp32", "x_faces_stage2"): {"unit": "face", "f32": 10041.3, "f64": 141.3, "winstr": 8601},
     ("wenoz_ns", "fp32", "y_faces_stage2"): {"unit": "face", "f32": 9604.9, "f64": 141.3, "winstr": 8192},
-    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 256.0},
-    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 36.0, "f64": 40.0, "bytes": 352.0},
+    ("wenoz_ns", "fp32", "update_stage1"): {"unit": "cell", "f32": 84.0, "f64": 0.0, "bytes": 224.0},
+    ("wenoz_ns", "fp32", "update_stage2"): {"unit": "cell", "f32": 44.0, "f64": 24.0, "bytes": 320.0},
 }
 HBM_FALLBACK_GBS = 6800.0
 

@@ -82,7 +82,7 @@ struct FaceArgs32 {
   const float* M;      // mirror [hi (nv planes) | lo (nv planes) | ...]
   const float* Mn;     // mirrored gradient along the face normal [nv][ny][nx]
   const double* W;     // FP64 state [nv][ny][nx] (stage 1: reference fluxes and cell differences)
-  void* out;           // face buffer (two FP64 blocks, then four FP32 blocks; see ld_face64)
+  void* out;           // face buffer (one FP64 block, then five FP32 blocks; see ld_face64)
   const double* dtp;
   unsigned int* status;
   int nx, ny, bcx, bcy;
@@ -96,7 +96,7 @@ struct FaceArgs32 {
 // FP32-bulk cell update: FP64 accumulation; writes the next mirror.
 struct UpdateArgs32 {
   double* W;           // FP64 state [W | Wx (| Wy)][nv][ny][nx]: W^n read and W^{n+1} written (stage 2)
-  float* fx;           // x-face buffer (two FP64 blocks, then four FP32 blocks; see write_face32)
+  float* fx;           // x-face buffer (one FP64 block, then five FP32 blocks; see write_face32)
   float* fy;           // y-face buffer (2D)
   float* M;            // FP32 mirror: W^n / W* / W^{n+1} (hi, lo, Wx, Wy planes)
   int nx, ny, bcx, bcy;

@@ -11,9 +11,11 @@
 // A face evaluates dF = F - F_Euler(W_ref), F_t, W0 - W_ref, W_t and W_tt in single
 // precision and writes its flux parts once, in FP64, with the FP64 reference flux added
 // (write_face32), and its interface-value parts as single-precision deltas from W_ref; the
-// cell update adds W_ref back, so the MSMD accumulation of cell averages and slopes, and
-// conservation, stay in FP64.  The time-integration coefficients of the exponential terms
-// are FP64 (gks_device.cuh).
+// cell update adds W_ref back, so the MSMD accumulation of the cell averages, and
+// conservation, stay in FP64.  The slopes at the new time level are difference quotients of
+// interface values, formed afresh each step from the FP64 cell difference (rounded) and the
+// single-precision interface deltas; they are computed in single precision.  The
+// time-integration coefficients of the exponential terms are FP64 (gks_device.cuh).
 #pragma once
 #include "gks_kernels.cuh"
 #include "gks_sweep.cuh"
@@ -32,6 +34,13 @@ __device__ __forceinline__ double f2d_int(float f) {
   unsigned hi = sgn | (ed << 20) | (m >> 3), lo = m << 29;
   if (e == 0u) { hi = sgn; lo = 0u; }
   return __hiloint2double((int)hi, (int)lo);
+}
+
+// f with a subnormal value flushed to zero of the same sign: the float that f2d_int maps to a
+// double which converts back to the same float.
+__device__ __forceinline__ float ftz_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x7f800000u) ? f : __uint_as_float(b & 0x80000000u);
 }
 
 // double -> float rounded to nearest (ties to even) on the integer pipes: for results in the
@@ -122,10 +131,11 @@ __device__ __forceinline__ long mirror_at(int q, int v, long c, long ncell) {
   return DIM == 2 ? 4 * ((long)q * ncell + c) + v : ((long)q * 3 + v) * ncell + c;
 }
 
-// Face buffer of the FP32-bulk form: two FP64 blocks (k = 0 Xi, 1 dW), then four FP32 blocks
-// (q = 0 dOmega, 1 dLT, 2 A, 3 D), each nfaces long.  In 2D each block is face-major, a face's
-// four variables contiguous (two 128-bit accesses for the FP64 blocks, one for the FP32
-// ones); in 1D each block is three planes.
+// Face buffer of the FP32-bulk form: one FP64 block (k = 0 Xi), then five FP32 blocks (q = 0
+// dOmega, 1 dLT, 2 A, 3 D, 4 dW), each nfaces long; the FP32 blocks start at FP64 index
+// N nfaces (face32_base).  In 2D each block is face-major, a face's four variables contiguous
+// (two 128-bit accesses for the FP64 block, one for each FP32 one); in 1D each block is three
+// planes.
 template <int DIM, bool CG>
 __device__ __forceinline__ void ld_face64(const double* o64, int k, long face, long nfaces, double* v) {
   if constexpr (DIM == 2) {
@@ -167,6 +177,14 @@ __device__ __forceinline__ void st_face32(float* o32, int q, long face, long nfa
   }
 }
 template <int DIM>
+__device__ __forceinline__ float* face32_base(double* o64, long nfaces) {
+  return reinterpret_cast<float*>(o64 + (long)(DIM + 2) * nfaces);
+}
+template <int DIM>
+__device__ __forceinline__ const float* face32_base(const double* o64, long nfaces) {
+  return reinterpret_cast<const float*>(o64 + (long)(DIM + 2) * nfaces);
+}
+template <int DIM>
 __device__ __forceinline__ long face64_at(int k, long face, long nfaces) {
   return DIM == 2 ? 4 * ((long)k * nfaces + face) : (long)k * 3 * nfaces + face;
 }
@@ -187,7 +205,7 @@ __device__ __forceinline__ void prefetch_face_epilogue(const FaceArgs32& a, int 
     for (int v = 0; v < N; ++v) { prefetch_line<CG>(a.W + v * ncell + cl); prefetch_line<CG>(a.W + v * ncell + cr); }
   } else {
     const double* o64 = static_cast<const double*>(a.out);
-    const float* o32 = reinterpret_cast<const float*>(o64 + 2L * N * nfaces);
+    const float* o32 = face32_base<DIM>(o64, nfaces);
     if constexpr (DIM == 2) {   // a face's Xi and dLT lie in one line each
       prefetch_line<CG>(o64 + face64_at<DIM>(0, face, nfaces));
       prefetch_line<CG>(o32 + face32_at<DIM>(1, face, nfaces));
@@ -216,13 +234,13 @@ __device__ __forceinline__ void euler_flux64(const double* W, double gamma, doub
   F[N - 1] = (W[N - 1] + p) * un;
 }
 
-// Face outputs of the FP32-bulk sweeps.  The face buffer holds two FP64 blocks, then four FP32
+// Face outputs of the FP32-bulk sweeps.  The face buffer holds one FP64 block, then five FP32
 // blocks (layout at ld_face64: per face and block, the variables contiguous in 2D):
 //   FP64 Xi  = dt F_ref + (dt dF + dt^2/6 F_t)           (stage 1; stage 2 adds dt^2/3 F_t*)
-//   FP64 dW  = W_right - W_left of the face's two cells    (stage 1)
 //   FP32 dOmega = W0 - W_ref + dt/2 W_t + dt^2/8 W_tt     (stage 1)
 //   FP32 dLT = W0 - W_ref + dt W_t + dt^2/6 W_tt          (stage 1; stage 2 adds dt^2/3 W_tt*)
 //   FP32 A = dt/2 dF + dt^2/8 F_t,  D = dt/2 dFc - A       (stage 1; read by the stage-1 update)
+//   FP32 dW  = W_right - W_left of the face's two cells, the FP64 difference rounded (stage 1)
 // F_ref = F_Euler(W_left) in FP64 (W_ref = W_left is the face's reference state), dF and F_t the
 // single-precision flux delta and derivative, dFc = F_Euler(W_right) - F_Euler(W_left) in the
 // single-precision delta form.  Xi is one FP64 value per face, so its differences across a
@@ -241,7 +259,7 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
   const int N = DIM + 2;
   const long ncell = (long)a.nx * a.ny;
   double* o64 = static_cast<double*>(a.out);
-  float* o32 = reinterpret_cast<float*>(o64 + 2L * N * nfaces);
+  float* o32 = face32_base<DIM>(o64, nfaces);
   const StepTimes* tc = a.tc;
   const int stage = STAGE ? STAGE : a.stage;
   if (stage == 1) {
@@ -266,7 +284,8 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
     if (mr) wr[1 + DIR] = -wr[1 + DIR];
     euler_flux64<DIM, DIR>(wl, a.P.gamma, Fref);
     const double dt = ldd<CG>(&tc->dt);
-    double xi[N], dw[N];
+    double xi[N];
+    float dw[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       // at a wall face every flux but that of the wall-normal momentum is an odd function
@@ -275,10 +294,10 @@ __device__ __forceinline__ void write_face32(const FaceArgs32& a, long face, lon
       // (conservation of mass, energy and tangential momentum stays exact)
       const bool odd_at_wall = (ml || mr) && v != 1 + DIR;
       xi[v] = odd_at_wall ? 0.0 : fma(dt, Fref[v], f2d_int(dpsi[v]));
-      dw[v] = wr[v] - wl[v];
+      dw[v] = __double2float_rn(wr[v] - wl[v]);   // the sweep is issue-bound: one conversion
     }
     st_face64<DIM>(o64, 0, face, nfaces, xi);
-    st_face64<DIM>(o64, 1, face, nfaces, dw);
+    st_face32<DIM>(o32, 4, face, nfaces, dw);
   } else {
     const float s3f = ldf<CG>(&tc->s3f);
     double xi[N];
@@ -684,11 +703,12 @@ faces_2d_f32_kernel(FaceArgs32 a) {
 //     of W^n plus the single-precision increment -(A_{i+1/2} + D_{i-1/2})/dx - (..)/dy, added
 //     exactly (two-sum) and renormalised; the W* slopes (dW + dOmega_{i+1/2} - dOmega_{i-1/2})/dx
 //     as floats.
-//   Stage 2: W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy and the slopes
-//     W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx, accumulated in FP64, written in
-//     place (each cell reads only its own state), and the mirror of W^{n+1} exactly as
-//     write_mirror builds it from the FP64 state (hi/lo of W, the slopes rounded to float), so
-//     a run restarted from its FP64 state continues bit for bit.
+//   Stage 2: W^{n+1} = W^n - (Xi_{i+1/2} - Xi_{i-1/2})/dx - (..)/dy accumulated in FP64 and
+//     the slopes W_x^{n+1} = (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2})/dx in single precision
+//     (stored as their exact FP64 images), written in place (each cell reads only its own
+//     state), and the mirror of W^{n+1} exactly as write_mirror builds it from the FP64 state
+//     (hi/lo of W, the slopes rounded to float), so a run restarted from its FP64 state
+//     continues bit for bit.
 // ---------------------------------------------------------------------------
 // FP32 mirror of one cell's FP64 state: W as hi/lo float pairs, the slopes as floats.
 // Store one cell's mirror blocks (hi, lo, x slope, y slope; the y slope unused in 1D).
@@ -754,10 +774,10 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   const long L = N * ncell;
   const double* x64 = reinterpret_cast<const double*>(a.fx);
   const double* y64 = reinterpret_cast<const double*>(a.fy);
-  float* x32 = a.fx + 4L * N * nfx;   // after the 2N FP64 planes
-  float* y32 = DIM == 2 ? a.fy + 4L * N * nfy : nullptr;
+  float* x32 = a.fx + 2L * N * nfx;   // after the FP64 block (N values per face)
+  float* y32 = DIM == 2 ? a.fy + 2L * N * nfy : nullptr;
   const double idx = a.idx, idy = a.idy;
-  const float idxf = (float)idx, idyf = (float)idy;
+  const float idxf = d2f_int(idx), idyf = d2f_int(idy);
   float* M = a.M;
   if (STAGE == 1) {
     // all loads first
@@ -770,24 +790,17 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
 #pragma unroll
       for (int v = 0; v < N; ++v) { h0[v] = M[mirror_at<1>(0, v, c, ncell)]; lo0[v] = M[mirror_at<1>(1, v, c, ncell)]; }
     }
-    {
-      double d[N];
-      ld_face32<DIM, CG>(x32, 0, fxl, nfx, Ol);
-      ld_face32<DIM, CG>(x32, 0, fxl + 1, nfx, Or);
-      ld_face32<DIM, CG>(x32, 2, fxl + 1, nfx, Ax);
-      ld_face32<DIM, CG>(x32, 3, fxl, nfx, Dxv);
-      ld_face64<DIM, CG>(x64, 1, fxl, nfx, d);
-#pragma unroll
-      for (int v = 0; v < N; ++v) dWx[v] = (float)d[v];
-      if (DIM == 2) {
-        ld_face32<DIM, CG>(y32, 0, fyb, nfy, Ob);
-        ld_face32<DIM, CG>(y32, 0, fyt, nfy, Ot);
-        ld_face32<DIM, CG>(y32, 2, fyt, nfy, Ay);
-        ld_face32<DIM, CG>(y32, 3, fyb, nfy, Dyv);
-        ld_face64<DIM, CG>(y64, 1, fyb, nfy, d);
-#pragma unroll
-        for (int v = 0; v < N; ++v) dWy[v] = (float)d[v];
-      }
+    ld_face32<DIM, CG>(x32, 0, fxl, nfx, Ol);
+    ld_face32<DIM, CG>(x32, 0, fxl + 1, nfx, Or);
+    ld_face32<DIM, CG>(x32, 2, fxl + 1, nfx, Ax);
+    ld_face32<DIM, CG>(x32, 3, fxl, nfx, Dxv);
+    ld_face32<DIM, CG>(x32, 4, fxl, nfx, dWx);
+    if (DIM == 2) {
+      ld_face32<DIM, CG>(y32, 0, fyb, nfy, Ob);
+      ld_face32<DIM, CG>(y32, 0, fyt, nfy, Ot);
+      ld_face32<DIM, CG>(y32, 2, fyt, nfy, Ay);
+      ld_face32<DIM, CG>(y32, 3, fyb, nfy, Dyv);
+      ld_face32<DIM, CG>(y32, 4, fyb, nfy, dWy);
     }
     float mh[N], ml[N], mx[N], my[N];   // the W* mirror of this cell
 #pragma unroll
@@ -813,44 +826,40 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
     store_mirror<DIM>(M, c, ncell, mh, ml, mx, my);
   } else {
     // all loads first, then the FP64 accumulation and the stores
-    double W0[N], Xl[N], Xr[N], dWx[N], Yb[N], Yt[N], dWy[N];
-    float dLx[N], dLy[N];
+    double W0[N], Xl[N], Xr[N], Yb[N], Yt[N];
+    float dWx[N], lxl[N], lxr[N], dWy[N], lyb[N], lyt[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) W0[v] = ldd<CG>(a.W + v * ncell + c);
-    {
-      float l0[N], l1[N];
-      ld_face64<DIM, CG>(x64, 0, fxl, nfx, Xl);
-      ld_face64<DIM, CG>(x64, 0, fxl + 1, nfx, Xr);
-      ld_face64<DIM, CG>(x64, 1, fxl, nfx, dWx);
-      ld_face32<DIM, CG>(x32, 1, fxl + 1, nfx, l1);
-      ld_face32<DIM, CG>(x32, 1, fxl, nfx, l0);
-#pragma unroll
-      for (int v = 0; v < N; ++v) dLx[v] = l1[v] - l0[v];
-      if (DIM == 2) {
-        ld_face64<DIM, CG>(y64, 0, fyb, nfy, Yb);
-        ld_face64<DIM, CG>(y64, 0, fyt, nfy, Yt);
-        ld_face64<DIM, CG>(y64, 1, fyb, nfy, dWy);
-        ld_face32<DIM, CG>(y32, 1, fyt, nfy, l1);
-        ld_face32<DIM, CG>(y32, 1, fyb, nfy, l0);
-#pragma unroll
-        for (int v = 0; v < N; ++v) dLy[v] = l1[v] - l0[v];
-      }
+    ld_face64<DIM, CG>(x64, 0, fxl, nfx, Xl);
+    ld_face64<DIM, CG>(x64, 0, fxl + 1, nfx, Xr);
+    ld_face32<DIM, CG>(x32, 4, fxl, nfx, dWx);
+    ld_face32<DIM, CG>(x32, 1, fxl + 1, nfx, lxr);
+    ld_face32<DIM, CG>(x32, 1, fxl, nfx, lxl);
+    if (DIM == 2) {
+      ld_face64<DIM, CG>(y64, 0, fyb, nfy, Yb);
+      ld_face64<DIM, CG>(y64, 0, fyt, nfy, Yt);
+      ld_face32<DIM, CG>(y32, 4, fyb, nfy, dWy);
+      ld_face32<DIM, CG>(y32, 1, fyt, nfy, lyt);
+      ld_face32<DIM, CG>(y32, 1, fyb, nfy, lyb);
     }
     float mh[N], ml[N], mx[N], my[N];   // the W^{n+1} mirror of this cell
 #pragma unroll
     for (int v = 0; v < N; ++v) {
-      // the slopes (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2}) / dx in FP64, and their float
-      // mirror as the FP64 slope rounded (the mirror write_mirror would build from the state)
+      // The slopes (dW_{i-1/2} + dLT_{i+1/2} - dLT_{i-1/2}) / dx in single precision: each
+      // is a fresh difference quotient of interface values (nothing accumulates in it), its
+      // dLT parts are single-precision results, and the sweeps read it only as a float.  The
+      // state keeps it as the exact FP64 image of its float (subnormals flushed to zero), so
+      // the float mirror is again a function of the FP64 state.
       double w = W0[v] - (Xr[v] - Xl[v]) * idx;
-      const double sx = fma(dWx[v], idx, f2d_int(dLx[v] * idxf));
-      a.W[L + v * ncell + c] = sx;
-      mx[v] = d2f_int(sx);
+      const float sx = ftz_int((dWx[v] + (lxr[v] - lxl[v])) * idxf);
+      a.W[L + v * ncell + c] = f2d_int(sx);
+      mx[v] = sx;
       my[v] = 0.f;
       if (DIM == 2) {
         w -= (Yt[v] - Yb[v]) * idy;
-        const double sy = fma(dWy[v], idy, f2d_int(dLy[v] * idyf));
-        a.W[2 * L + v * ncell + c] = sy;
-        my[v] = d2f_int(sy);
+        const float sy = ftz_int((dWy[v] + (lyt[v] - lyb[v])) * idyf);
+        a.W[2 * L + v * ncell + c] = f2d_int(sy);
+        my[v] = sy;
       }
       a.W[v * ncell + c] = w;
       split_hilo(w, mh[v], ml[v]);
@@ -859,8 +868,12 @@ __device__ __forceinline__ void update_f32_cell(const UpdateArgs32& a, long c) {
   }
 }
 
+// Four blocks of 256 threads per SM (64 registers): the stage-2 update issues all of a cell's
+// loads before its FP64 arithmetic, and the extra warps overlap one cell's FP64 work with
+// other cells' loads (0.244 against 0.281 ms at 2048^2 with three blocks and 80 registers,
+// despite 24 B of spills).
 template <int DIM, int STAGE>
-__global__ void __launch_bounds__(256, 3) update_f32_kernel(UpdateArgs32 a) {
+__global__ void __launch_bounds__(256, 4) update_f32_kernel(UpdateArgs32 a) {
   update_f32_cell<DIM, STAGE, false>(a, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
