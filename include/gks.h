@@ -301,7 +301,8 @@ void gks_batch_destroy(gks_batch* b);
  * library holds it until the process exits.  Larger nx is rejected with GKS_EINVAL.
  * The call allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
  * The first call on a device looks up the array's device address on that device; make
- * that first call before any stream capture.  With lazy module loading
+ * that first call before any stream capture.  The call itself cannot be captured into a
+ * CUDA graph: it synchronises `stream` and reads its status word back to the host.  With lazy module loading
  * (CUDA_MODULE_LOADING=LAZY) the driver places the array in device memory when the
  * library's module is first loaded on a device, which can be that first call: callers that
  * must not allocate after start-up make the first call during start-up.  gamma, mu, Pr,
