@@ -62,7 +62,9 @@ enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1, GKS_BC_REFLECTING = 2, GKS_
  * GKS_PREC_FP32_BULK: reconstruction, WENO-Z and gas-kinetic arithmetic of the face sweeps in
  * FP32 on differences from a reference cell (the state mirrored as float hi/lo pairs); the
  * time-integration coefficients of the exponential terms and the MSMD accumulation of cell
- * averages and slopes in FP64 (conservation is exact). */
+ * averages in FP64 (conservation is exact); the slopes at the new time level, difference
+ * quotients of interface values formed afresh each step, in FP32 (kept in the FP64 state
+ * as the exact images of their floats). */
 enum { GKS_PREC_FP64 = 0, GKS_PREC_FP32_BULK = 1 };
 
 typedef struct gks_opts {
