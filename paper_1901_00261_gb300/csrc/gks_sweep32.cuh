@@ -25,8 +25,9 @@ namespace gks {
 // float -> double on the integer pipes: the exponent rebiased (127 -> 1023) and the 23
 // significand bits moved to the top of the 52; exact for normal floats, inf and nan, and
 // zero; subnormal floats (|f| < 2^-126) become zero of the same sign.  The FP64 pipe also
-// executes FP32 -> FP64 conversions and bounds the stage-2 update; the face epilogues and
-// the updates convert their single-precision parts with this instead.
+// executes FP32 -> FP64 conversions and is busy in the stage-2 update and the stage-1
+// sweeps; the face epilogues and the updates convert their single-precision parts with this
+// instead.
 __device__ __forceinline__ double f2d_int(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
